@@ -1,0 +1,239 @@
+/*
+ * vx.h — C ABI of the GB300-native periodic vertex model.
+ *
+ * The library computes, on one GPU, the hot path of a confluent periodic 2D
+ * vertex model (VertAX, arXiv 2604.06896): cell areas and perimeters, edge
+ * lengths, the energy
+ *
+ *     E(X) = sum_cells K_A (A - A0)^2 + K_P (P - P0)^2 + sum_edges Lambda l
+ *
+ * (Methods, "Vertex model formulation": the E1 form with per-cell moduli plus
+ * the line-tension term of E2), its analytic gradient on the 3-valent
+ * vertices, relaxation to force balance by FIRE or gradient descent with T1
+ * transitions (Methods, "Simulation engine", "T1 transitions"), and the
+ * gradient of an outer cost taken at the equilibrium, by the implicit adjoint
+ * (Methods, "Implicit differentiation") or by equilibrium propagation
+ * (Methods, "Equilibrium propagation").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns a vx_status and never throws across the ABI.  On
+ *   an error, vx_last_error() returns a message for the calling thread.
+ * - Arguments are validated before anything is launched; an invalid argument
+ *   leaves every output untouched.
+ * - "dev" pointers are CUDA device pointers on the current device, "host"
+ *   pointers are ordinary (pageable or pinned) host memory.  The caller owns
+ *   every buffer it passes; the library never frees them.  A vx_tissue owns
+ *   its device topology and workspace, allocated in vx_tissue_create and
+ *   released by vx_tissue_destroy.
+ * - Positions X are float64 [V][2] (x, y interleaved).  Forces and gradients
+ *   are float64.  The compute precision is chosen per tissue (VX_F64 or
+ *   VX_F32: FP32 arithmetic on hi/lo FP32 position pairs, FP64 reductions).
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls that return results to the host synchronise it.
+ *
+ * Topology format (Methods, "System state and data structure")
+ * ------------------------------------------------------------
+ *   he      int32 [HE][8]: prev, next, twin, source, target, face, offx, offy
+ *           (offx, offy in {-1, 0, 1}: the target vertex sits at
+ *           X[target] + (offx Lx, offy Ly) as seen from the source)
+ *   face_he int32 [n]: one half-edge of each face
+ *   edge_id int32 [HE]: the undirected edge of each half-edge, 0 .. E-1
+ * A periodic Voronoi tessellation of n generic seeds has V = 2n vertices,
+ * E = 3n edges and HE = 6n half-edges.
+ */
+#ifndef VX_H
+#define VX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VX_OK = 0,
+  VX_NOT_CONVERGED = 1,      /* non-fatal: outputs hold the last iterate   */
+  VX_ERR_INVALID_ARG = 2,
+  VX_ERR_DEGENERATE_SEEDS = 3,
+  VX_ERR_CUDA = 4,
+  VX_ERR_OOM = 5,
+  VX_ERR_INDEFINITE = 6,     /* CG met p^T H p <= 0 (non-convex energy)    */
+  VX_ERR_TIMEOUT = 7,
+  VX_ERR_NONFINITE = 8,      /* NaN or Inf met in positions or forces      */
+  VX_ERR_TOPOLOGY = 9        /* T1 bookkeeping found an inconsistency      */
+} vx_status;
+
+enum { VX_F64 = 0, VX_F32 = 1 };
+enum { VX_FIRE = 0, VX_GD = 1 };
+enum { VX_ADJOINT_CG = 0, VX_EP_CENTERED = 1, VX_EP_FORWARD = 2 };
+enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
+enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2 };
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* vx_last_error(void);
+
+/* Library version, e.g. "vx 0.1 sm_103a". */
+const char* vx_version(void);
+
+/*
+ * vx_build_mesh — periodic Voronoi tessellation of n seeds (host only).
+ *
+ * Methods, "Mesh initialization" and "Periodic mode": the tessellation of the
+ * seeds on the torus [0,Lx) x [0,Ly); every polygon of a primary seed is
+ * kept, and half-edges crossing the box get the offset of their target.
+ * Indexing is canonical (identical for identical seeds on any machine):
+ *   face alpha = seed alpha; a vertex is a Delaunay triangle of the torus,
+ *   keyed by its three (seed, image shift) corners in CCW order, translated
+ *   so that the first corner has shift 0, smallest rotation first; vertices
+ *   are numbered by increasing key; a vertex sits at the circumcentre of its
+ *   key triangle wrapped into the box; the half-edges of each face are
+ *   contiguous (faces in order), counter-clockwise from the face's smallest
+ *   vertex index; an edge's id is the rank of its smaller half-edge index.
+ *
+ * seeds_xy  host float64 [n][2], each in [0,Lx) x [0,Ly)
+ * n_cells   n >= 3
+ * vert_xy   host float64 [2n][2]   (out)
+ * he        host int32 [6n][8]     (out)
+ * face_he   host int32 [n]         (out; the first half-edge of each face)
+ * edge_id   host int32 [6n]        (out)
+ * Returns VX_ERR_DEGENERATE_SEEDS when four seeds are (nearly) cocircular
+ * (a Voronoi edge shorter than 1e-9 sqrt(Lx Ly / n)), when a cell touches
+ * its own periodic image, or when a cell spans more than one box copy.
+ */
+vx_status vx_build_mesh(const double* seeds_xy, int32_t n_cells, double Lx, double Ly,
+                        double* vert_xy, int32_t* he, int32_t* face_he, int32_t* edge_id);
+
+/* Opaque handle: one tissue (topology on the device + workspace). */
+typedef struct vx_tissue_s* vx_tissue;
+
+/*
+ * vx_tissue_create — upload a topology and allocate the workspace.
+ * he, face_he, edge_id: host tables in the format above (any valid
+ * 3-valent periodic half-edge mesh, not only canonical ones).
+ * dtype: VX_F64 or VX_F32.  The handle is bound to the current device.
+ */
+vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                           int32_t n_cells, int32_t n_half_edges, double Lx, double Ly,
+                           int32_t dtype, void* stream, vx_tissue* out);
+vx_status vx_tissue_destroy(vx_tissue t);
+
+/* Sizes of a tissue: cells, vertices, edges, half-edges. */
+vx_status vx_tissue_sizes(vx_tissue t, int32_t* n_cells, int32_t* n_vertices,
+                          int32_t* n_edges, int32_t* n_half_edges);
+
+/*
+ * vx_tissue_topology — copy the tissue's current topology (T1 transitions
+ * made by vx_minimize change it) back to host tables of the input format.
+ * Half-edge and edge identities are kept through T1 transitions.
+ */
+vx_status vx_tissue_topology(vx_tissue t, int32_t* he, int32_t* face_he, int32_t* edge_id);
+
+/*
+ * Model parameters.  Each pointer is a device float64 array (K_A, K_P, A0,
+ * P0 per cell [n]; lambda per edge [E]) or NULL, in which case the scalar
+ * beside it is used for every cell / edge.
+ */
+typedef struct {
+  const double* KA;  const double* KP;  const double* A0;  const double* P0;
+  const double* lambda;
+  double KA_s, KP_s, A0_s, P0_s, lambda_s;
+} vx_params;
+
+/*
+ * vx_energy_forces — energy and forces at X.
+ * Energy: Methods, "Vertex model formulation"; forces F = -grad_X E
+ * (Results, "Energy functions").
+ * X  dev float64 [V][2]; F dev float64 [V][2] or NULL; E dev float64 [1] or
+ * NULL.  Asynchronous on `stream`; deterministic (no atomics).
+ */
+vx_status vx_energy_forces(vx_tissue t, const double* X, const vx_params* p,
+                           double* F, double* E, void* stream);
+
+/* Inner minimiser options (defaults from vx_min_opts_default). */
+typedef struct {
+  int32_t method;      /* VX_FIRE or VX_GD                                  */
+  double  tol;         /* stop when max_i |F_i| < tol ...                   */
+  int32_t patience;    /* ... for this many consecutive iterations         */
+  int32_t max_iter;
+  double  gd_lr;       /* gradient-descent step eta                         */
+  double  dt0, dt_max; /* FIRE time steps                                   */
+  int32_t n_min;       /* FIRE N_min                                        */
+  double  f_inc, f_dec, alpha0, f_alpha;
+  double  l_min;       /* T1 threshold; <= 0 disables T1 checks             */
+  int32_t path;        /* VX_PATH_AUTO / RESIDENT / PLAIN                   */
+  int32_t check_every; /* PLAIN path: host polls convergence every k steps  */
+} vx_min_opts;
+
+typedef struct {
+  int32_t status;      /* VX_OK or VX_NOT_CONVERGED (or an error)           */
+  int32_t iters;       /* position updates made                             */
+  int32_t n_t1, n_stretch;
+  int32_t n_short_edges; /* edges shorter than l_min at the end             */
+  int32_t n_inverted;  /* cells with A <= 0 at the end                      */
+  double  fmax;        /* max_i |F_i| at the returned X                     */
+  double  energy;
+  int32_t path_used;   /* VX_PATH_RESIDENT or VX_PATH_PLAIN                 */
+  int32_t force_evals;
+} vx_min_result;
+
+void vx_min_opts_default(vx_min_opts* o);
+
+/*
+ * vx_minimize — relax X to force balance (Methods, "Simulation engine"):
+ * FIRE (Bitzek et al., PRL 97, 170201, 2006; unit masses, semi-implicit
+ * Euler step) or gradient descent X <- X - eta grad E; stop rule
+ * max_i |F_i| < tol for `patience` consecutive iterations, or max_iter.
+ * Each iteration first checks the edges for T1 transitions (Methods, "T1
+ * transitions"; both candidates at length 1.5 l_min, lower energy kept).
+ * X dev float64 [V][2], in/out; positions stay unwrapped (the offsets are
+ * kept consistent).  r host (out).  Synchronises `stream`.
+ */
+vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
+                      vx_min_result* r, void* stream);
+
+/* Outer-gradient options. */
+typedef struct {
+  int32_t mode;        /* VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD      */
+  double  beta;        /* EP nudging strength                               */
+  double  cg_rtol;     /* CG stops at |r| <= cg_rtol |b|                    */
+  int32_t cg_max_iter;
+  int32_t cost;        /* built-in cost for EP (and for adjoint if dCdX NULL) */
+  const double* cost_data; /* dev: X_target [V][2] (v2v) or q_target [2]     */
+  vx_min_opts inner;   /* nudged phases (T1 is not applied in them)          */
+} vx_grad_opts;
+
+typedef struct {
+  int32_t status;
+  int32_t cg_iters;
+  double  cg_rel_residual;
+  double  cost;        /* C at X* (built-in costs)                          */
+  int32_t nudged_iters[2];
+} vx_grad_result;
+
+void vx_grad_opts_default(vx_grad_opts* o);
+
+/*
+ * vx_equilibrium_grad — gradient of an outer cost C(X*) with respect to the
+ * line tensions Lambda_e and the targets A0, P0 at an equilibrium X*.
+ * VX_ADJOINT_CG (Methods, "Implicit differentiation", adjoint form):
+ *   solve H lam = Pi grad_X C by conjugate gradients on a Hessian-vector
+ *   product (Pi removes the two rigid translations, the null space of H),
+ *   then g_theta = -(d^2 E / dX dtheta)^T lam.
+ * VX_EP_CENTERED / VX_EP_FORWARD (Methods, "Equilibrium propagation"):
+ *   re-minimise E +/- (beta/2) C (or E + beta C and the free X*) from X*,
+ *   nudging with the translation-free part of grad_X C, and difference
+ *   d_theta E over beta.
+ * Xstar dev float64 [V][2]; dCdX dev float64 [V][2] (adjoint; NULL uses the
+ * built-in cost).  g_lambda dev [E], g_A0 dev [n], g_P0 dev [n], each may be
+ * NULL.  r host (out).  Synchronises `stream`.
+ */
+vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params* p,
+                              const double* dCdX, const vx_grad_opts* o,
+                              double* g_lambda, double* g_A0, double* g_P0,
+                              vx_grad_result* r, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VX_H */

@@ -1,0 +1,276 @@
+"""GB300-native periodic vertex model (VertAX hot path) — Python binding.
+
+The names follow the C ABI of ``include/vx.h``.  This module only marshals
+arguments: torch tensors (float64, contiguous, on the current CUDA device)
+are passed to the CUDA library as raw device pointers on torch's current
+stream.  There is no CPU fallback; importing fails when ``libvx.so`` has not
+been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _capi as capi
+from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # noqa: F401
+                    VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
+                    VX_PATH_AUTO, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
+
+__all__ = ["vx_build_mesh", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
+           "vx_equilibrium_grad", "Tissue", "EquilibriumFn", "VxError"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev_f64(x, shape=None):
+    torch = _torch()
+    if not torch.is_tensor(x):
+        x = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(x.shape)}")
+    return x
+
+
+# ---------------------------------------------------------------- mesh
+
+def vx_build_mesh(seeds, Lx, Ly):
+    """Periodic Voronoi tessellation of the seeds (host; see vx.h).
+    Returns dict(vert [2n,2] f64, he [6n,8] i32, face_he [n] i32,
+    edge_id [6n] i32, n, Lx, Ly) as numpy arrays."""
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64))
+    n = s.shape[0]
+    vert = np.zeros((2 * n, 2), dtype=np.float64)
+    he = np.zeros((6 * n, 8), dtype=np.int32)
+    face_he = np.zeros(n, dtype=np.int32)
+    edge_id = np.zeros(6 * n, dtype=np.int32)
+    st = capi.vx_build_mesh(s.ctypes.data, n, float(Lx), float(Ly), vert.ctypes.data,
+                            he.ctypes.data, face_he.ctypes.data, edge_id.ctypes.data)
+    capi.check(st, "vx_build_mesh")
+    return dict(vert=vert, he=he, face_he=face_he, edge_id=edge_id, n=n, Lx=float(Lx),
+                Ly=float(Ly))
+
+
+# ------------------------------------------------------------ parameters
+
+def make_params(p, n=None, E=None):
+    """vx_params from a dict with KA, KP, A0, P0 (scalar or per-cell) and lam
+    (scalar or per-edge).  Returns (struct, tensors kept alive)."""
+    keep = []
+    out = capi.vx_params()
+    for key, fp, fs, size in (("KA", "KA", "KA_s", n), ("KP", "KP", "KP_s", n),
+                              ("A0", "A0", "A0_s", n), ("P0", "P0", "P0_s", n),
+                              ("lam", "lambda_", "lambda_s", E)):
+        v = p[key]
+        if np.ndim(v) == 0 and not (hasattr(v, "dim") and v.dim() > 0):
+            setattr(out, fp, None)
+            setattr(out, fs, float(v))
+        else:
+            t = _dev_f64(v)
+            if size is not None and t.numel() != size:
+                raise ValueError(f"{key}: expected {size} values, got {t.numel()}")
+            keep.append(t)
+            setattr(out, fp, t.data_ptr())
+            setattr(out, fs, 0.0)
+    return out, keep
+
+
+@dataclass
+class MinResult:
+    status: int
+    iters: int
+    n_t1: int
+    n_stretch: int
+    n_short_edges: int
+    n_inverted: int
+    fmax: float
+    energy: float
+    path_used: int
+    force_evals: int
+
+    @property
+    def converged(self):
+        return self.status == capi.VX_OK
+
+
+def min_opts(**kw):
+    o = capi.vx_min_opts()
+    capi.vx_min_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "method" and isinstance(v, str):
+            v = {"fire": VX_FIRE, "gd": VX_GD}[v]
+        if k == "path" and isinstance(v, str):
+            v = {"auto": VX_PATH_AUTO, "resident": VX_PATH_RESIDENT, "plain": VX_PATH_PLAIN}[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown minimiser option {k}")
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------------- tissue
+
+class Tissue:
+    """A tissue handle (vx_tissue): device topology plus workspace."""
+
+    def __init__(self, mesh, dtype="f64"):
+        he = np.ascontiguousarray(mesh["he"], dtype=np.int32)
+        face_he = np.ascontiguousarray(mesh["face_he"], dtype=np.int32)
+        edge_id = np.ascontiguousarray(mesh["edge_id"], dtype=np.int32)
+        self.n = int(face_he.shape[0])
+        self.HE = int(he.shape[0])
+        self.V, self.E = self.HE // 3, self.HE // 2
+        self.Lx, self.Ly = float(mesh["Lx"]), float(mesh["Ly"])
+        self.dtype = {"f64": VX_F64, "f32": VX_F32}[dtype] if isinstance(dtype, str) else dtype
+        h = C.c_void_p()
+        _torch().cuda.init()
+        st = capi.vx_tissue_create(he.ctypes.data, face_he.ctypes.data, edge_id.ctypes.data,
+                                   self.n, self.HE, self.Lx, self.Ly, self.dtype, _stream(),
+                                   C.byref(h))
+        capi.check(st, "vx_tissue_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            capi.vx_tissue_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def topology(self):
+        he = np.zeros((self.HE, 8), dtype=np.int32)
+        face_he = np.zeros(self.n, dtype=np.int32)
+        edge_id = np.zeros(self.HE, dtype=np.int32)
+        capi.check(capi.vx_tissue_topology(self.handle, he.ctypes.data, face_he.ctypes.data,
+                                           edge_id.ctypes.data), "vx_tissue_topology")
+        return dict(he=he, face_he=face_he, edge_id=edge_id, n=self.n, Lx=self.Lx, Ly=self.Ly)
+
+
+def vx_tissue_create(mesh, dtype="f64"):
+    return Tissue(mesh, dtype)
+
+
+def vx_energy_forces(t: Tissue, X, params, forces=True, energy=True):
+    """(F [V,2] f64 or None, E [1] f64 or None) at X, on the current stream."""
+    torch = _torch()
+    X = _dev_f64(X, (t.V, 2))
+    prm, keep = make_params(params, t.n, t.E)
+    F = torch.empty((t.V, 2), dtype=torch.float64, device="cuda") if forces else None
+    E = torch.empty(1, dtype=torch.float64, device="cuda") if energy else None
+    st = capi.vx_energy_forces(t.handle, _ptr(X), C.byref(prm), _ptr(F), _ptr(E), _stream())
+    capi.check(st, "vx_energy_forces")
+    return F, E
+
+
+def vx_minimize(t: Tissue, X, params, **opts):
+    """Relax X (device f64 [V,2], updated in place) to force balance."""
+    if not (hasattr(X, "is_cuda") and X.is_cuda and X.dtype == _torch().float64
+            and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (updated in place)")
+    prm, keep = make_params(params, t.n, t.E)
+    o = min_opts(**opts)
+    r = capi.vx_min_result()
+    st = capi.vx_minimize(t.handle, _ptr(X), C.byref(prm), C.byref(o), C.byref(r), _stream())
+    capi.check(st, "vx_minimize")
+    return MinResult(r.status, r.iters, r.n_t1, r.n_stretch, r.n_short_edges, r.n_inverted,
+                     r.fmax, r.energy, r.path_used, r.force_evals)
+
+
+@dataclass
+class GradResult:
+    status: int
+    cg_iters: int
+    cg_rel_residual: float
+    cost: float
+    nudged_iters: tuple
+
+
+def vx_equilibrium_grad(t: Tissue, Xstar, params, dCdX=None, mode=VX_ADJOINT_CG, beta=1e-3,
+                        cg_rtol=1e-10, cg_max_iter=20000, cost=VX_COST_NONE, cost_data=None,
+                        inner=None):
+    """Gradient of the outer cost at the equilibrium X* with respect to
+    (Lambda, A0, P0).  Returns (dict of device f64 tensors, GradResult)."""
+    torch = _torch()
+    Xstar = _dev_f64(Xstar, (t.V, 2))
+    prm, keep = make_params(params, t.n, t.E)
+    o = capi.vx_grad_opts()
+    capi.vx_grad_opts_default(C.byref(o))
+    o.mode, o.beta, o.cg_rtol, o.cg_max_iter, o.cost = mode, beta, cg_rtol, cg_max_iter, cost
+    cd = None
+    if cost_data is not None:
+        cd = _dev_f64(cost_data)
+        o.cost_data = cd.data_ptr()
+    if inner is not None:
+        o.inner = min_opts(**inner)
+    dc = _dev_f64(dCdX, (t.V, 2)) if dCdX is not None else None
+    g = {k: torch.empty(m, dtype=torch.float64, device="cuda")
+         for k, m in (("lam", t.E), ("A0", t.n), ("P0", t.n))}
+    r = capi.vx_grad_result()
+    st = capi.vx_equilibrium_grad(t.handle, _ptr(Xstar), C.byref(prm), _ptr(dc), C.byref(o),
+                                  _ptr(g["lam"]), _ptr(g["A0"]), _ptr(g["P0"]), C.byref(r),
+                                  _stream())
+    capi.check(st, "vx_equilibrium_grad")
+    return g, GradResult(r.status, r.cg_iters, r.cg_rel_residual, r.cost, tuple(r.nudged_iters))
+
+
+def _make_equilibrium_fn():
+    torch = _torch()
+
+    class EquilibriumFn(torch.autograd.Function):
+        """X* = argmin_X E(X; Lambda, A0, P0) as a differentiable function.
+
+        forward: vx_minimize from X0.  backward: the implicit adjoint, i.e.
+        vx_equilibrium_grad(ADJOINT_CG) with dC/dX* = grad_output.  Gradients
+        flow to lam (per edge), A0 and P0 (per cell); X0 gets none (X* does
+        not depend on the starting point within its basin).
+        """
+
+        @staticmethod
+        def forward(ctx, X0, lam, A0, P0, tissue, KA, KP, opts):
+            X = X0.detach().clone().contiguous()
+            params = dict(KA=KA, KP=KP, A0=A0.detach(), P0=P0.detach(), lam=lam.detach())
+            res = vx_minimize(tissue, X, params, **(opts or {}))
+            ctx.tissue, ctx.KA, ctx.KP = tissue, KA, KP
+            ctx.save_for_backward(X, lam.detach(), A0.detach(), P0.detach())
+            ctx.result = res
+            return X
+
+        @staticmethod
+        def backward(ctx, gX):
+            X, lam, A0, P0 = ctx.saved_tensors
+            params = dict(KA=ctx.KA, KP=ctx.KP, A0=A0, P0=P0, lam=lam)
+            g, _ = vx_equilibrium_grad(ctx.tissue, X, params, dCdX=gX.contiguous())
+            return None, g["lam"], g["A0"], g["P0"], None, None, None, None
+
+    return EquilibriumFn
+
+
+class _Lazy:
+    _fn = None
+
+    def __getattr__(self, k):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_equilibrium_fn()
+        return getattr(_Lazy._fn, k)
+
+
+EquilibriumFn = _Lazy()

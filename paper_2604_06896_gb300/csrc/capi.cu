@@ -1,0 +1,421 @@
+// The extern "C" entry points of vx.h: argument validation, the tissue
+// handle, and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tissue.h"
+#include "vx_internal.h"
+
+namespace vx {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace vx
+
+using vx::set_error;
+
+#define VX_CUDA_TRY(expr)                                                        \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));             \
+      return e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA;         \
+    }                                                                            \
+  } while (0)
+
+namespace {
+
+vx_status invalid(const std::string& m) {
+  set_error(m);
+  return VX_ERR_INVALID_ARG;
+}
+
+// Checks that (he, face_he, edge_id) is a 3-valent periodic half-edge mesh
+// with n faces; returns "" when valid.
+std::string check_tables(const int32_t* he, const int32_t* face_he, const int32_t* edge_id, int n,
+                         int HE) {
+  if (n < 1) return "n_cells must be positive";
+  if (HE != 6 * n) return "a 3-valent tessellation of the torus has 6 n half-edges";
+  const int V = HE / 3, E = HE / 2;
+  std::vector<int> outdeg(V, 0), ecount(E, 0);
+  for (int h = 0; h < HE; ++h) {
+    const int32_t* r = he + 8 * h;
+    for (int k = 0; k < 5; ++k) {
+      const int lim = (k < 3) ? HE : V;
+      if (r[k] < 0 || r[k] >= lim) return "he[" + std::to_string(h) + "] index out of range";
+    }
+    if (r[5] < 0 || r[5] >= n) return "he[" + std::to_string(h) + "] face out of range";
+    if (r[6] < -1 || r[6] > 1 || r[7] < -1 || r[7] > 1) return "offsets must be in {-1, 0, 1}";
+    if (edge_id[h] < 0 || edge_id[h] >= E) return "edge_id out of range";
+    ecount[edge_id[h]]++;
+    outdeg[r[3]]++;
+  }
+  for (int h = 0; h < HE; ++h) {
+    const int32_t* r = he + 8 * h;
+    const int32_t* tw = he + 8 * r[2];
+    if (r[2] == h || tw[2] != h) return "twin is not an involution at " + std::to_string(h);
+    if (tw[3] != r[4] || tw[4] != r[3]) return "twin endpoints do not match";
+    if (tw[6] != -r[6] || tw[7] != -r[7]) return "twin offsets must be negated";
+    if (he[8 * r[1] + 0] != h) return "prev(next(h)) != h";
+    if (he[8 * r[1] + 3] != r[4]) return "next(h) does not start at target(h)";
+    if (he[8 * r[1] + 5] != r[5]) return "next(h) lies in another face";
+    if (edge_id[r[2]] != edge_id[h]) return "twins must share an edge id";
+  }
+  for (int e = 0; e < E; ++e)
+    if (ecount[e] != 2) return "every edge id must own exactly two half-edges";
+  for (int v = 0; v < V; ++v)
+    if (outdeg[v] != 3) return "vertex " + std::to_string(v) + " is not 3-valent";
+  std::vector<char> seen(HE, 0);
+  for (int c = 0; c < n; ++c) {
+    const int h0 = face_he[c];
+    if (h0 < 0 || h0 >= HE || he[8 * h0 + 5] != c) return "face_he[" + std::to_string(c) + "]";
+    int h = h0, k = 0;
+    do {
+      if (seen[h]) return "a half-edge lies on two face cycles";
+      seen[h] = 1;
+      h = he[8 * h + 1];
+    } while (h != h0 && ++k < HE);
+    int ox = 0, oy = 0;
+    h = h0;
+    do {
+      ox += he[8 * h + 6];
+      oy += he[8 * h + 7];
+      h = he[8 * h + 1];
+    } while (h != h0);
+    if (ox || oy) return "offsets around face " + std::to_string(c) + " do not cancel";
+  }
+  for (int h = 0; h < HE; ++h)
+    if (!seen[h]) return "half-edge " + std::to_string(h) + " lies on no face cycle";
+  return "";
+}
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+bool params_ok(const vx_params* p, std::string* m) {
+  if (!p) {
+    *m = "params is NULL";
+    return false;
+  }
+  const double sc[5] = {p->KA_s, p->KP_s, p->A0_s, p->P0_s, p->lambda_s};
+  for (double x : sc)
+    if (!std::isfinite(x)) {
+      *m = "scalar parameters must be finite";
+      return false;
+    }
+  return true;
+}
+
+vx::ParamsD to_params(const vx_params* p) {
+  vx::ParamsD d;
+  d.KA = p->KA;
+  d.KP = p->KP;
+  d.A0 = p->A0;
+  d.P0 = p->P0;
+  d.lam = p->lambda;
+  d.KA_s = p->KA_s;
+  d.KP_s = p->KP_s;
+  d.A0_s = p->A0_s;
+  d.P0_s = p->P0_s;
+  d.lam_s = p->lambda_s;
+  return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vx_last_error(void) { return vx::g_err.c_str(); }
+
+const char* vx_version(void) { return "vx 0.1 sm_103a"; }
+
+vx_status vx_build_mesh(const double* seeds_xy, int32_t n_cells, double Lx, double Ly,
+                        double* vert_xy, int32_t* he, int32_t* face_he, int32_t* edge_id) {
+  if (!seeds_xy || !vert_xy || !he || !face_he || !edge_id) return invalid("NULL pointer");
+  if (n_cells < 3) return invalid("n_cells must be >= 3");
+  if (n_cells > (1 << 24)) return invalid("n_cells too large");
+  if (!(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
+    return invalid("box sides must be positive and finite");
+  for (int i = 0; i < n_cells; ++i) {
+    const double x = seeds_xy[2 * i], y = seeds_xy[2 * i + 1];
+    if (!(x >= 0 && x < Lx && y >= 0 && y < Ly)) return invalid("seeds must lie in [0,Lx) x [0,Ly)");
+  }
+  std::string err;
+  const vx_status s = vx::build_mesh(seeds_xy, n_cells, Lx, Ly, vert_xy, he, face_he, edge_id, &err);
+  if (s != VX_OK) set_error(err);
+  return s;
+}
+
+vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                           int32_t n_cells, int32_t n_half_edges, double Lx, double Ly,
+                           int32_t dtype, void* stream, vx_tissue* out) {
+  if (!he || !face_he || !edge_id || !out) return invalid("NULL pointer");
+  if (dtype != VX_F64 && dtype != VX_F32) return invalid("dtype must be VX_F64 or VX_F32");
+  if (!(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
+    return invalid("box sides must be positive and finite");
+  if (n_cells > (1 << 24)) return invalid("n_cells too large");
+  const std::string m = check_tables(he, face_he, edge_id, n_cells, n_half_edges);
+  if (!m.empty()) return invalid(m);
+  const int n = n_cells, HE = n_half_edges, V = HE / 3, E = HE / 2;
+  vx_tissue_s* t = new vx_tissue_s();
+  cudaGetDevice(&t->device);
+  t->n = n;
+  t->V = V;
+  t->E = E;
+  t->HE = HE;
+  t->Lx = Lx;
+  t->Ly = Ly;
+  t->dtype = dtype;
+  t->ext2int.resize(HE);
+  t->int2ext.resize(HE);
+  for (int h = 0; h < HE; ++h) {
+    const int tw = he[8 * h + 2];
+    const int hi = 2 * edge_id[h] + (h > tw ? 1 : 0);
+    t->ext2int[h] = hi;
+    t->int2ext[hi] = h;
+  }
+  std::vector<uint32_t> tgt(HE);
+  std::vector<int32_t> nxt(HE), face(HE), vout(3 * V, -1), ff(n);
+  std::vector<int> firstout(V, -1);
+  for (int hc = 0; hc < HE; ++hc) {
+    const int32_t* r = he + 8 * hc;
+    const int hi = t->ext2int[hc];
+    tgt[hi] = vx::pack_tgt(r[4], r[6], r[7]);
+    nxt[hi] = t->ext2int[r[1]];
+    face[hi] = r[5];
+    const int s = r[3];
+    if (firstout[s] < 0 || hi < firstout[s]) firstout[s] = hi;
+  }
+  // Out-lists in counter-clockwise order: h, twin(prev(h)), twin(prev(.)).
+  for (int v = 0; v < V; ++v) {
+    int h = firstout[v];
+    for (int a = 0; a < 3; ++a) {
+      vout[a * V + v] = h;
+      const int hp = t->ext2int[he[8 * t->int2ext[h] + 0]];
+      h = hp ^ 1;
+    }
+    if (h != firstout[v]) {
+      delete t;
+      return invalid("vertex " + std::to_string(v) + ": out-half-edges do not close");
+    }
+  }
+  for (int c = 0; c < n; ++c) ff[c] = t->ext2int[face_he[c]];
+  auto bytes = [](size_t b) { return b < 16 ? (size_t)16 : b; };
+  const int nbc = (n + 255) / 256 + 1, nbv = (V + 255) / 256 + 1;
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&t->tgt, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->nxt, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->face, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->vout, bytes(12 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->ffirst, bytes(4 * (size_t)n));
+  if (e == cudaSuccess) e = cudaMalloc(&t->Xw, bytes(16 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->vel, bytes(16 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->F, bytes(16 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->cellc, bytes(16 * (size_t)n));
+  if (e == cudaSuccess) e = cudaMalloc(&t->shortbits, bytes(4 * (size_t)(E / 32 + 1)));
+  if (e == cudaSuccess) e = cudaMalloc(&t->touched, bytes(4 * (size_t)(V / 32 + 1)));
+  if (e == cudaSuccess) e = cudaMalloc(&t->partE, bytes(3 * 8 * (size_t)nbc));
+  if (e == cudaSuccess) e = cudaMalloc(&t->partF, bytes(4 * 8 * (size_t)nbv));
+  if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(vx::FireCtrl));
+  if (e == cudaSuccess) e = cudaMalloc(&t->dout, sizeof(vx::MinOut));
+  t->work = nullptr;
+  t->work_doubles = 0;
+  if (e != cudaSuccess) {
+    vx_tissue_destroy(t);
+    set_error(std::string("vx_tissue_create: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA;
+  }
+  cudaStream_t s = as_stream(stream);
+  VX_CUDA_TRY(cudaMemcpyAsync(t->tgt, tgt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->nxt, nxt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->face, face.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->vout, vout.data(), 12 * (size_t)V, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemsetAsync(t->shortbits, 0, 4 * (size_t)(E / 32 + 1), s));
+  VX_CUDA_TRY(cudaMemsetAsync(t->touched, 0, 4 * (size_t)(V / 32 + 1), s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = t;
+  return VX_OK;
+}
+
+vx_status vx_tissue_destroy(vx_tissue t) {
+  if (!t) return VX_OK;
+  void* ptrs[] = {t->tgt, t->nxt,       t->face,    t->vout,  t->ffirst, t->Xw,
+                  t->vel, t->F,         t->cellc,   t->shortbits, t->touched, t->partE,
+                  t->partF, t->ctrl,    t->dout,    t->work};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete t;
+  return VX_OK;
+}
+
+vx_status vx_tissue_sizes(vx_tissue t, int32_t* n_cells, int32_t* n_vertices, int32_t* n_edges,
+                          int32_t* n_half_edges) {
+  if (!t) return invalid("NULL tissue");
+  if (n_cells) *n_cells = t->n;
+  if (n_vertices) *n_vertices = t->V;
+  if (n_edges) *n_edges = t->E;
+  if (n_half_edges) *n_half_edges = t->HE;
+  return VX_OK;
+}
+
+vx_status vx_tissue_topology(vx_tissue t, int32_t* he, int32_t* face_he, int32_t* edge_id) {
+  if (!t || !he || !face_he || !edge_id) return invalid("NULL pointer");
+  const int HE = t->HE, V = t->V, n = t->n;
+  std::vector<uint32_t> tgt(HE);
+  std::vector<int32_t> nxt(HE), face(HE), vout(3 * V), ff(n);
+  VX_CUDA_TRY(cudaMemcpy(tgt.data(), t->tgt, 4 * (size_t)HE, cudaMemcpyDeviceToHost));
+  VX_CUDA_TRY(cudaMemcpy(nxt.data(), t->nxt, 4 * (size_t)HE, cudaMemcpyDeviceToHost));
+  VX_CUDA_TRY(cudaMemcpy(face.data(), t->face, 4 * (size_t)HE, cudaMemcpyDeviceToHost));
+  VX_CUDA_TRY(cudaMemcpy(vout.data(), t->vout, 12 * (size_t)V, cudaMemcpyDeviceToHost));
+  VX_CUDA_TRY(cudaMemcpy(ff.data(), t->ffirst, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  for (int hi = 0; hi < HE; ++hi) {
+    const int s = vx::tgt_v(tgt[hi ^ 1]);
+    int slot = 0;
+    while (slot < 3 && vout[slot * V + s] != hi) ++slot;
+    if (slot == 3) {
+      set_error("device topology is inconsistent");
+      return VX_ERR_TOPOLOGY;
+    }
+    const int prev = vout[((slot + 1) % 3) * V + s] ^ 1;
+    int32_t* r = he + 8 * t->int2ext[hi];
+    r[0] = t->int2ext[prev];
+    r[1] = t->int2ext[nxt[hi]];
+    r[2] = t->int2ext[hi ^ 1];
+    r[3] = s;
+    r[4] = vx::tgt_v(tgt[hi]);
+    r[5] = face[hi];
+    r[6] = vx::tgt_ox(tgt[hi]);
+    r[7] = vx::tgt_oy(tgt[hi]);
+    edge_id[t->int2ext[hi]] = hi >> 1;
+  }
+  for (int c = 0; c < n; ++c) face_he[c] = t->int2ext[ff[c]];
+  return VX_OK;
+}
+
+vx_status vx_energy_forces(vx_tissue t, const double* X, const vx_params* p, double* F, double* E,
+                           void* stream) {
+  if (!t || !X) return invalid("NULL tissue or X");
+  std::string m;
+  if (!params_ok(p, &m)) return invalid(m);
+  const vx_status s = vx::energy_forces(t, X, to_params(p), F, E, as_stream(stream));
+  if (s != VX_OK) set_error(std::string("vx_energy_forces: ") + cudaGetErrorString(cudaGetLastError()));
+  return s;
+}
+
+void vx_min_opts_default(vx_min_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = VX_FIRE;
+  o->tol = 1e-8;
+  o->patience = 1;
+  o->max_iter = 100000;
+  o->gd_lr = 1e-2;
+  o->dt0 = 0.01;
+  o->dt_max = 0.5;
+  o->n_min = 5;
+  o->f_inc = 1.1;
+  o->f_dec = 0.5;
+  o->alpha0 = 0.1;
+  o->f_alpha = 0.99;
+  o->l_min = 0.0;
+  o->path = VX_PATH_AUTO;
+  o->check_every = 50;
+}
+
+static bool min_opts_ok(const vx_min_opts* o, std::string* m) {
+  if (!o) {
+    *m = "opts is NULL";
+    return false;
+  }
+  if (o->method != VX_FIRE && o->method != VX_GD) *m = "method must be VX_FIRE or VX_GD";
+  else if (!(o->tol >= 0)) *m = "tol must be >= 0";
+  else if (o->patience < 1) *m = "patience must be >= 1";
+  else if (o->max_iter < 0) *m = "max_iter must be >= 0";
+  else if (!(o->dt0 > 0) || !(o->dt_max > 0)) *m = "dt0 and dt_max must be positive";
+  else if (!(o->gd_lr > 0)) *m = "gd_lr must be positive";
+  else if (o->path < VX_PATH_AUTO || o->path > VX_PATH_PLAIN) *m = "unknown path";
+  else return true;
+  return false;
+}
+
+static vx::MinParams to_min_params(const vx_min_opts* o) {
+  vx::MinParams mp = {};
+  mp.method = o->method;
+  mp.tol = o->tol;
+  mp.patience = o->patience;
+  mp.max_iter = o->max_iter;
+  mp.gd_lr = o->gd_lr;
+  mp.dt0 = o->dt0;
+  mp.dt_max = o->dt_max;
+  mp.n_min = o->n_min;
+  mp.f_inc = o->f_inc;
+  mp.f_dec = o->f_dec;
+  mp.alpha0 = o->alpha0;
+  mp.f_alpha = o->f_alpha;
+  mp.l_min = o->l_min;
+  return mp;
+}
+
+vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
+                      vx_min_result* r, void* stream) {
+  if (!t || !X || !r) return invalid("NULL tissue, X or result");
+  std::string m;
+  if (!params_ok(p, &m) || !min_opts_ok(o, &m)) return invalid(m);
+  vx::MinOut out = {};
+  int used = 0;
+  const vx_status s = vx::minimize(t, X, to_params(p), to_min_params(o), o->path, o->check_every,
+                                   &out, &used, as_stream(stream));
+  if (s != VX_OK) {
+    if (s == VX_ERR_INVALID_ARG) set_error("the tissue does not fit one CTA's shared memory");
+    else set_error(std::string("vx_minimize: ") + cudaGetErrorString(cudaGetLastError()));
+    return s;
+  }
+  r->status = out.status;
+  r->iters = out.iters;
+  r->n_t1 = out.n_t1;
+  r->n_stretch = out.n_stretch;
+  r->n_short_edges = out.n_short;
+  r->n_inverted = out.n_inverted;
+  r->fmax = out.fmax;
+  r->energy = out.energy;
+  r->path_used = used;
+  r->force_evals = out.force_evals;
+  return (vx_status)out.status == VX_ERR_NONFINITE ? VX_ERR_NONFINITE : VX_OK;
+}
+
+void vx_grad_opts_default(vx_grad_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = VX_ADJOINT_CG;
+  o->beta = 1e-3;
+  o->cg_rtol = 1e-10;
+  o->cg_max_iter = 20000;
+  o->cost = VX_COST_NONE;
+  o->cost_data = nullptr;
+  vx_min_opts_default(&o->inner);
+  o->inner.tol = 1e-10;
+}
+
+vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params* p,
+                              const double* dCdX, const vx_grad_opts* o, double* g_lambda,
+                              double* g_A0, double* g_P0, vx_grad_result* r, void* stream) {
+  if (!t || !Xstar || !o || !r) return invalid("NULL tissue, X*, opts or result");
+  std::string m;
+  if (!params_ok(p, &m)) return invalid(m);
+  if (o->mode != VX_ADJOINT_CG && o->mode != VX_EP_CENTERED && o->mode != VX_EP_FORWARD)
+    return invalid("unknown gradient mode");
+  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_NONE)
+    return invalid("adjoint needs dCdX or a built-in cost");
+  if (o->mode != VX_ADJOINT_CG && o->cost == VX_COST_NONE)
+    return invalid("equilibrium propagation needs a built-in cost");
+  if (o->cost != VX_COST_NONE && !o->cost_data) return invalid("cost_data is NULL");
+  if (o->mode != VX_ADJOINT_CG && !(o->beta > 0)) return invalid("beta must be positive");
+  if (!min_opts_ok(&o->inner, &m)) return invalid(m);
+  return vx::equilibrium_grad(t, Xstar, to_params(p), dCdX, o, g_lambda, g_A0, g_P0, r,
+                              as_stream(stream));
+}
+
+}  // extern "C"

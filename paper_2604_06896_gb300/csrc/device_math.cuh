@@ -1,0 +1,468 @@
+// Device-side arithmetic of the periodic vertex model, shared by the
+// shared-memory-resident persistent kernels and the global-memory kernels.
+//
+// Geometry (Methods, "Vertex model formulation", "Periodic mode"):
+//   a half-edge h runs from X[src] to X[tgt] + (offx Lx, offy Ly);
+//   A_c = 1/2 sum cross(q_k, q_{k+1}) over the corners of cell c in a frame
+//   local to the cell's first corner, P_c = sum |q_{k+1} - q_k|;
+//   E = sum_c K_A (A - A0)^2 + K_P (P - P0)^2 + sum_e Lambda_e l_e.
+// Forces on a 3-valent vertex i with outgoing half-edges h_0, h_1, h_2
+// (counter-clockwise; cell c_a lies between h_a and h_{a+1}; edge a is shared
+// by c_a and c_{a-1}), d_a the edge vector and u_a = d_a / l_a:
+//   F_i = sum_a (Lambda_a + cP_{c_a} + cP_{c_{a-1}}) u_a
+//         - 1/2 sum_a cA_{c_a} rot(d_a - d_{a+1}),   rot(x, y) = (y, -x),
+// with cA = 2 K_A (A - A0) and cP = 2 K_P (P - P0) per cell.
+//
+// Internal half-edge numbering: edge e owns half-edges 2e and 2e + 1 (twin =
+// h ^ 1), 2e being the one with the smaller index in the caller's table.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+namespace vx {
+
+constexpr uint32_t kTgtMask = (1u << 28) - 1;
+
+__host__ __device__ inline uint32_t pack_tgt(int v, int ox, int oy) {
+  return (uint32_t)v | ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
+}
+__host__ __device__ inline int tgt_v(uint32_t t) { return (int)(t & kTgtMask); }
+__host__ __device__ inline int tgt_ox(uint32_t t) { return (int)((t >> 28) & 3u) - 1; }
+__host__ __device__ inline int tgt_oy(uint32_t t) { return (int)((t >> 30) & 3u) - 1; }
+
+// ------------------------------------------------------------ precisions
+
+// Error of s = fl(a + b) (Knuth's TwoSum; exact in round-to-nearest).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bb = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct PolF64 {
+  using R = double;
+  using Pos = double2;
+  struct Box { double Lx, Ly; };
+  static __host__ __device__ Box make_box(double Lx, double Ly) { return Box{Lx, Ly}; }
+  static __device__ __forceinline__ void diff(const Pos& t, const Pos& s, int ox, int oy,
+                                              const Box& b, R& dx, R& dy) {
+    dx = (t.x + ox * b.Lx) - s.x;
+    dy = (t.y + oy * b.Ly) - s.y;
+  }
+  static __device__ __forceinline__ void add(Pos& p, R dx, R dy) {
+    p.x += dx;
+    p.y += dy;
+  }
+  static __device__ __forceinline__ double2 to_d(const Pos& p) { return p; }
+  static __device__ __forceinline__ Pos from_d(double x, double y) { return make_double2(x, y); }
+  static __device__ __forceinline__ R rsqrt(R x) { return 1.0 / sqrt(x); }
+};
+
+// FP32 arithmetic on positions held as unevaluated hi + lo float pairs, so
+// that differences of nearby vertices keep ~48 bits and the force tolerance is
+// not limited by the absolute-coordinate quantum of one float.
+struct PolF32 {
+  using R = float;
+  using Pos = float4;  // (hi.x, hi.y, lo.x, lo.y)
+  struct Box { float Lxh, Lxl, Lyh, Lyl; };
+  static __host__ __device__ Box make_box(double Lx, double Ly) {
+    Box b;
+    b.Lxh = (float)Lx;
+    b.Lxl = (float)(Lx - (double)b.Lxh);
+    b.Lyh = (float)Ly;
+    b.Lyl = (float)(Ly - (double)b.Lyh);
+    return b;
+  }
+  // a_hi + a_lo - b_hi - b_lo + o (Lh + Ll), rounded once at the end.
+  static __device__ __forceinline__ float dd(float ah, float al, float bh, float bl, int o,
+                                             float Lh, float Ll) {
+    const float s = __fsub_rn(ah, bh);
+    const float e = two_sum_err(ah, -bh, s);
+    const float oL = (float)o * Lh;            // exact: o in {-2..2}
+    const float t = __fadd_rn(s, oL);
+    const float e2 = two_sum_err(s, oL, t);
+    return __fadd_rn(t, __fadd_rn(__fadd_rn(e, e2), __fadd_rn(__fsub_rn(al, bl), (float)o * Ll)));
+  }
+  static __device__ __forceinline__ void diff(const Pos& t, const Pos& s, int ox, int oy,
+                                              const Box& b, R& dx, R& dy) {
+    dx = dd(t.x, t.z, s.x, s.z, ox, b.Lxh, b.Lxl);
+    dy = dd(t.y, t.w, s.y, s.w, oy, b.Lyh, b.Lyl);
+  }
+  static __device__ __forceinline__ void add1(float& hi, float& lo, float d) {
+    const float s = __fadd_rn(hi, d);
+    const float e = two_sum_err(hi, d, s);
+    const float l = __fadd_rn(lo, e);
+    const float h2 = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(h2, s));
+    hi = h2;
+  }
+  static __device__ __forceinline__ void add(Pos& p, R dx, R dy) {
+    add1(p.x, p.z, dx);
+    add1(p.y, p.w, dy);
+  }
+  static __device__ __forceinline__ double2 to_d(const Pos& p) {
+    return make_double2((double)p.x + (double)p.z, (double)p.y + (double)p.w);
+  }
+  static __device__ __forceinline__ Pos from_d(double x, double y) {
+    const float hx = (float)x, hy = (float)y;
+    return make_float4(hx, hy, (float)(x - (double)hx), (float)(y - (double)hy));
+  }
+  static __device__ __forceinline__ R rsqrt(R x) { return rsqrtf(x); }
+};
+
+// ------------------------------------------------------------ views
+
+// Pointers to one tissue's topology and state.  The pointers may address
+// shared or global memory: the same code runs in both residencies.
+template <class P>
+struct View {
+  using R = typename P::R;
+  using Pos = typename P::Pos;
+  Pos* X;
+  uint32_t* tgt;    // [HE]
+  int32_t* nxt;     // [HE]
+  int32_t* face;    // [HE]
+  int32_t* vout;    // [3][V] (SoA)
+  int32_t* ffirst;  // [n]
+  int n, V, E;
+  typename P::Box box;
+  double Lx, Ly;
+};
+
+// Parameters as the caller gave them (float64, per cell / per edge or
+// uniform).
+struct ParamsD {
+  const double *KA, *KP, *A0, *P0, *lam;
+  double KA_s, KP_s, A0_s, P0_s, lam_s;
+  __device__ __forceinline__ double ka(int c) const { return KA ? KA[c] : KA_s; }
+  __device__ __forceinline__ double kp(int c) const { return KP ? KP[c] : KP_s; }
+  __device__ __forceinline__ double a0(int c) const { return A0 ? A0[c] : A0_s; }
+  __device__ __forceinline__ double p0(int c) const { return P0 ? P0[c] : P0_s; }
+  __device__ __forceinline__ double la(int e) const { return lam ? lam[e] : lam_s; }
+};
+
+template <class P>
+__device__ __forceinline__ int src_of(const View<P>& v, int h) {
+  return tgt_v(v.tgt[h ^ 1]);
+}
+
+// Area and perimeter of cell c; lengths below lmin flag their edge in
+// `shortbits` (lmin <= 0 disables the check).  Returns whether any edge of
+// the cell was flagged.
+template <class P>
+__device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename P::R& A,
+                                              typename P::R& Per, typename P::R lmin,
+                                              uint32_t* shortbits, double* eline = nullptr,
+                                              const ParamsD* prm = nullptr) {
+  using R = typename P::R;
+  const int h0 = v.ffirst[c];
+  const int v0 = src_of(v, h0);
+  const typename P::Pos X0 = v.X[v0];
+  R qx = 0, qy = 0, A2 = 0, pp = 0;
+  int cx = 0, cy = 0;
+  int h = h0;
+  bool flagged = false;
+  double el = 0.0;
+  int guard = 0;
+  do {
+    const uint32_t tg = v.tgt[h];
+    cx += tgt_ox(tg);
+    cy += tgt_oy(tg);
+    R nx, ny;
+    P::diff(v.X[tgt_v(tg)], X0, cx, cy, v.box, nx, ny);
+    A2 += qx * ny - nx * qy;
+    const R ex = nx - qx, ey = ny - qy;
+    const R l = sqrt(ex * ex + ey * ey);
+    pp += l;
+    if (l < lmin) {
+      atomicOr(&shortbits[h >> 6], 1u << ((h >> 1) & 31));
+      flagged = true;
+    }
+    if (eline) el += 0.5 * prm->la(h >> 1) * (double)l;
+    qx = nx;
+    qy = ny;
+    h = v.nxt[h];
+  } while (h != h0 && ++guard < 4096);
+  A = (R)0.5 * A2;
+  Per = pp;
+  if (eline) *eline = el;
+  return flagged;
+}
+
+// Force on vertex i from the cell coefficients (cA, cP) and edge tensions.
+template <class P, class CellC, class LamT>
+__device__ __forceinline__ void vertex_force(const View<P>& v, int i, const CellC* cellc,
+                                             const LamT* lam, double lam_s, typename P::R& fx,
+                                             typename P::R& fy) {
+  using R = typename P::R;
+  const typename P::Pos Xi = v.X[i];
+  R dx[3], dy[3], ux[3], uy[3], cA[3], cP[3], la[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int h = v.vout[a * v.V + i];
+    const uint32_t tg = v.tgt[h];
+    P::diff(v.X[tgt_v(tg)], Xi, tgt_ox(tg), tgt_oy(tg), v.box, dx[a], dy[a]);
+    const R r = P::rsqrt(dx[a] * dx[a] + dy[a] * dy[a]);
+    ux[a] = dx[a] * r;
+    uy[a] = dy[a] * r;
+    const CellC cc = cellc[v.face[h]];
+    cA[a] = (R)cc.x;
+    cP[a] = (R)cc.y;
+    la[a] = lam ? (R)lam[h >> 1] : (R)lam_s;
+  }
+  R gx = 0, gy = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int am = (a + 2) % 3, ap = (a + 1) % 3;
+    const R T = la[a] + cP[a] + cP[am];
+    gx += T * ux[a];
+    gy += T * uy[a];
+    // -1/2 cA rot(d_a - d_{a+1}),  rot(x, y) = (y, -x)
+    const R wx = dx[a] - dx[ap], wy = dy[a] - dy[ap];
+    gx -= (R)0.5 * cA[a] * wy;
+    gy += (R)0.5 * cA[a] * wx;
+  }
+  fx = gx;
+  fy = gy;
+}
+
+// ------------------------------------------------------------ T1 (serial)
+
+// Slot of half-edge h in the out-list of its source vertex s.
+template <class P>
+__device__ __forceinline__ int out_slot(const View<P>& v, int s, int h) {
+  return (v.vout[s] == h) ? 0 : (v.vout[v.V + s] == h ? 1 : 2);
+}
+// prev(h): the twin of the out-half-edge after h (counter-clockwise).
+template <class P>
+__device__ __forceinline__ int prev_of(const View<P>& v, int h) {
+  const int s = src_of(v, h);
+  const int k = out_slot(v, s, h);
+  return v.vout[((k + 1) % 3) * v.V + s] ^ 1;
+}
+
+template <class P>
+__device__ __forceinline__ void edge_vec_d(const View<P>& v, int h, double& dx, double& dy) {
+  const uint32_t tg = v.tgt[h];
+  const double2 a = P::to_d(v.X[src_of(v, h)]);
+  const double2 b = P::to_d(v.X[tgt_v(tg)]);
+  dx = (b.x + tgt_ox(tg) * v.Lx) - a.x;
+  dy = (b.y + tgt_oy(tg) * v.Ly) - a.y;
+}
+
+template <class P>
+__device__ __forceinline__ double edge_len_d(const View<P>& v, int h) {
+  double dx, dy;
+  edge_vec_d(v, h, dx, dy);
+  return sqrt(dx * dx + dy * dy);
+}
+
+template <class P>
+__device__ __forceinline__ int face_size(const View<P>& v, int h0) {
+  int k = 0, h = h0;
+  do {
+    ++k;
+    h = v.nxt[h];
+  } while (h != h0 && k < 4096);
+  return k;
+}
+
+// Cell energy K_A (A - A0)^2 + K_P (P - P0)^2 in float64 (for the T1
+// comparison).
+template <class P>
+__device__ double cell_energy_d(const View<P>& v, int c, const ParamsD& prm) {
+  const int h0 = v.ffirst[c];
+  const double2 X0 = P::to_d(v.X[src_of(v, h0)]);
+  double qx = 0, qy = 0, A2 = 0, pp = 0;
+  int cx = 0, cy = 0, h = h0, guard = 0;
+  do {
+    const uint32_t tg = v.tgt[h];
+    cx += tgt_ox(tg);
+    cy += tgt_oy(tg);
+    const double2 Xt = P::to_d(v.X[tgt_v(tg)]);
+    const double nx = (Xt.x + cx * v.Lx) - X0.x, ny = (Xt.y + cy * v.Ly) - X0.y;
+    A2 += qx * ny - nx * qy;
+    pp += sqrt((nx - qx) * (nx - qx) + (ny - qy) * (ny - qy));
+    qx = nx;
+    qy = ny;
+    h = v.nxt[h];
+  } while (h != h0 && ++guard < 4096);
+  const double A = 0.5 * A2, dA = A - prm.a0(c), dP = pp - prm.p0(c);
+  return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
+}
+
+struct T1Stats {
+  int n_t1, n_stretch, err;
+};
+
+constexpr double kT1Stretch = 1.5;  // both candidates: length 1.5 l_min
+
+// The serial T1 pass (Methods, "T1 transitions"): edges flagged in
+// `shortbits` are taken in increasing id, each re-checked against the current
+// positions; for an edge shorter than lmin the stretch and the T1 candidates
+// (both of length 1.5 lmin about the old midpoint) are compared by energy and
+// the lower one kept.  A T1 is not a candidate when a cell losing the edge is
+// a triangle, when the four cells are not distinct, or when an offset would
+// leave {-1, 0, 1}.  Edges with a larger id that a change makes short are
+// flagged and handled in the same pass.  Vertices of changed edges are
+// flagged in `touched` (their velocities are reset by the caller).  Clears
+// `shortbits`.  Cells whose geometry changed are appended to `dirty` (up to
+// `dirty_cap`; `*n_dirty` may exceed it).
+template <class P>
+__device__ __noinline__ void t1_pass(View<P> v, const ParamsD& prm, double lmin, uint32_t* shortbits,
+                        uint32_t* touched, T1Stats* st, int* dirty, int dirty_cap,
+                        int* n_dirty) {
+  using Pos = typename P::Pos;
+  const int nwords = (v.E + 31) >> 5;
+  const double lnew = kT1Stretch * lmin;
+  for (int w = 0; w < nwords; ++w) {
+    while (shortbits[w]) {
+      const uint32_t bits = shortbits[w];
+      const int bit = __ffs(bits) - 1;
+      shortbits[w] = bits & (bits - 1);
+      const int e = (w << 5) + bit;
+      const int h = 2 * e, hq = h ^ 1;
+      if (edge_len_d(v, h) >= lmin) continue;
+      const int a = src_of(v, h), b = tgt_v(v.tgt[h]);
+      touched[a >> 5] |= 1u << (a & 31);
+      touched[b >> 5] |= 1u << (b & 31);
+      const int C1 = v.face[h], C2 = v.face[hq];
+      const int hp1 = prev_of(v, h), hn1 = v.nxt[h];
+      const int hp2 = prev_of(v, hq), hn2 = v.nxt[hq];
+      const int ta_p = hp1 ^ 1, tb_y = hn1 ^ 1, tb_z = hp2 ^ 1, tx_a = hn2 ^ 1;
+      const int C3 = v.face[ta_p], C4 = v.face[tb_z];
+      const int cells[4] = {C1, C2, C3, C4};
+      const int hes[5] = {h, hp1, hn1, hp2, hn2};
+      // Images of the neighbours in a's frame (stored X = U - k L).
+      const uint32_t tg_h = v.tgt[h];
+      const int kbx = tgt_ox(tg_h), kby = tgt_oy(tg_h);
+      const int kpx = tgt_ox(v.tgt[ta_p]), kpy = tgt_oy(v.tgt[ta_p]);
+      const int kxx = tgt_ox(v.tgt[hn2]), kxy = tgt_oy(v.tgt[hn2]);
+      const int kyx = kbx + tgt_ox(v.tgt[hn1]), kyy = kby + tgt_oy(v.tgt[hn1]);
+      const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
+      bool allow = face_size(v, h) > 3 && face_size(v, hq) > 3 && C1 != C2 && C1 != C3 &&
+                   C1 != C4 && C2 != C3 && C2 != C4 && C3 != C4 && kyx >= -1 && kyx <= 1 &&
+                   kyy >= -1 && kyy <= 1 && kzx >= -1 && kzx <= 1 && kzy >= -1 && kzy <= 1;
+      // Geometry in a's frame.
+      double dx, dy;
+      edge_vec_d(v, h, dx, dy);
+      const double ell = sqrt(dx * dx + dy * dy);
+      const double ux = dx / ell, uy = dy / ell;
+      const double2 Xa = P::to_d(v.X[a]);
+      const double mx = Xa.x + 0.5 * dx, my = Xa.y + 0.5 * dy;
+      const Pos Xa0 = v.X[a], Xb0 = v.X[b];
+      // Candidate 1: stretch (b stays in its own frame).
+      const Pos Xas = P::from_d(mx - 0.5 * lnew * ux, my - 0.5 * lnew * uy);
+      const Pos Xbs = P::from_d(mx + 0.5 * lnew * ux - kbx * v.Lx, my + 0.5 * lnew * uy - kby * v.Ly);
+      v.X[a] = Xas;
+      v.X[b] = Xbs;
+      double Es = 0.0;
+      for (int k = 0; k < 4; ++k) Es += cell_energy_d(v, cells[k], prm);
+      for (int k = 0; k < 5; ++k) Es += prm.la(hes[k] >> 1) * edge_len_d(v, hes[k]);
+      bool take_t1 = false;
+      if (allow) {
+        // Save what a T1 rewrites.
+        const int sv_nxt_i[6] = {hp1, hp2, tx_a, hq, tb_y, h};
+        int sv_nxt[6];
+        for (int k = 0; k < 6; ++k) sv_nxt[k] = v.nxt[sv_nxt_i[k]];
+        const int sv_tgt_i[10] = {ta_p, hp1, hn1, tb_y, hn2, tx_a, tb_z, hp2, h, hq};
+        uint32_t sv_tgt[10];
+        for (int k = 0; k < 10; ++k) sv_tgt[k] = v.tgt[sv_tgt_i[k]];
+        const int sv_face[2] = {v.face[h], v.face[hq]};
+        int sv_vout[6];
+        for (int k = 0; k < 3; ++k) {
+          sv_vout[k] = v.vout[k * v.V + a];
+          sv_vout[3 + k] = v.vout[k * v.V + b];
+        }
+        const int sv_ff[2] = {v.ffirst[C1], v.ffirst[C2]};
+        const int p = tgt_v(v.tgt[ta_p]), y = tgt_v(v.tgt[hn1]);
+        const int x = tgt_v(v.tgt[hn2]), z = tgt_v(v.tgt[tb_z]);
+        // Candidate 2: T1.  a joins p and y on C1's side, b joins x and z.
+        const double px = -uy, py = ux;  // into C1
+        v.X[a] = P::from_d(mx + 0.5 * lnew * px, my + 0.5 * lnew * py);
+        v.X[b] = P::from_d(mx - 0.5 * lnew * px, my - 0.5 * lnew * py);
+        v.nxt[hp1] = hn1;
+        v.nxt[hp2] = hn2;
+        v.nxt[tx_a] = hq;
+        v.nxt[hq] = ta_p;
+        v.nxt[tb_y] = h;
+        v.nxt[h] = tb_z;
+        v.face[hq] = C3;
+        v.face[h] = C4;
+        v.tgt[ta_p] = pack_tgt(p, kpx, kpy);
+        v.tgt[hp1] = pack_tgt(a, -kpx, -kpy);
+        v.tgt[hn1] = pack_tgt(y, kyx, kyy);
+        v.tgt[tb_y] = pack_tgt(a, -kyx, -kyy);
+        v.tgt[hn2] = pack_tgt(x, kxx, kxy);
+        v.tgt[tx_a] = pack_tgt(b, -kxx, -kxy);
+        v.tgt[tb_z] = pack_tgt(z, kzx, kzy);
+        v.tgt[hp2] = pack_tgt(b, -kzx, -kzy);
+        v.tgt[h] = pack_tgt(b, 0, 0);
+        v.tgt[hq] = pack_tgt(a, 0, 0);
+        v.vout[a] = h;
+        v.vout[v.V + a] = hn1;
+        v.vout[2 * v.V + a] = ta_p;
+        v.vout[b] = hq;
+        v.vout[v.V + b] = hn2;
+        v.vout[2 * v.V + b] = tb_z;
+        if (v.ffirst[C1] == h) v.ffirst[C1] = hn1;
+        if (v.ffirst[C2] == hq) v.ffirst[C2] = hn2;
+        double Et = 0.0;
+        for (int k = 0; k < 4; ++k) Et += cell_energy_d(v, cells[k], prm);
+        for (int k = 0; k < 5; ++k) Et += prm.la(hes[k] >> 1) * edge_len_d(v, hes[k]);
+        if (Et < Es) {
+          take_t1 = true;
+        } else {
+          for (int k = 0; k < 6; ++k) v.nxt[sv_nxt_i[k]] = sv_nxt[k];
+          for (int k = 0; k < 10; ++k) v.tgt[sv_tgt_i[k]] = sv_tgt[k];
+          v.face[h] = sv_face[0];
+          v.face[hq] = sv_face[1];
+          for (int k = 0; k < 3; ++k) {
+            v.vout[k * v.V + a] = sv_vout[k];
+            v.vout[k * v.V + b] = sv_vout[3 + k];
+          }
+          v.ffirst[C1] = sv_ff[0];
+          v.ffirst[C2] = sv_ff[1];
+        }
+      }
+      if (take_t1) {
+        st->n_t1++;
+      } else {
+        v.X[a] = Xas;
+        v.X[b] = Xbs;
+        st->n_stretch++;
+      }
+      (void)Xa0;
+      (void)Xb0;
+      for (int k = 0; k < 4; ++k) {
+        if (*n_dirty < dirty_cap) dirty[*n_dirty] = cells[k];
+        ++*n_dirty;
+      }
+      // Edges at a or b with a larger id that are now short join this pass.
+      for (int s = 0; s < 2; ++s) {
+        const int vv = s ? b : a;
+        for (int k = 0; k < 3; ++k) {
+          const int hh = v.vout[k * v.V + vv];
+          const int f = hh >> 1;
+          if (f > e && edge_len_d(v, hh) < lmin) shortbits[f >> 5] |= 1u << (f & 31);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+}  // namespace vx

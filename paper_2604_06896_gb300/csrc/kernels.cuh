@@ -1,0 +1,49 @@
+// Kernel entry points and their host-side launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device_math.cuh"
+
+namespace vx {
+
+// Inner-minimiser parameters as the kernels see them.
+struct MinParams {
+  int method;  // 0 FIRE, 1 GD
+  double tol;
+  int patience, max_iter;
+  double gd_lr, dt0, dt_max;
+  int n_min;
+  double f_inc, f_dec, alpha0, f_alpha;
+  double l_min;
+  // Nudged phase of equilibrium propagation: force += -s Pi grad_X C.
+  int cost;              // 0 none, 1 v2v, 2 anisotropy
+  double nudge_s;
+  const double* cost_data;
+};
+
+// Control block of the global-memory minimiser (one per tissue).
+struct FireCtrl {
+  double dt, alpha;
+  int npos, below, it, done, status;
+  double P, FF, VV, fmax2;
+  double mixA, mixB, dt_step;
+  int zero_v;
+  unsigned int counter;
+  int any_short;
+  int n_t1, n_stretch;
+};
+
+// Result block written by the minimisers (device side).
+struct MinOut {
+  int status, iters, n_t1, n_stretch, n_short, n_inverted, force_evals, pad;
+  double fmax, energy;
+};
+
+template <class P>
+struct Workspace {
+  using R = typename P::R;
+  using R2 = typename std::conditional<std::is_same<R, double>::value, double2, float2>::type;
+};
+
+}  // namespace vx

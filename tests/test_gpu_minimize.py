@@ -1,0 +1,128 @@
+"""Inner minimiser: CUDA (resident and plain paths, through the C ABI)
+against the FP64 oracle.
+
+Equilibria are compared by an oracle polish (the oracle relaxes from the
+GPU's X* on the GPU's final topology): the displacement must stay below
+1e-4 sqrt(A0) and the oracle's max |F| at X_gpu is reported.  In FP64 the GPU
+and the oracle also follow the same trajectory (same T1 decisions, same
+iteration count).
+"""
+import numpy as np
+import pytest
+
+import vx_inputs as vi
+from oracle import mesh as omesh
+from oracle import model as omodel
+from oracle import solvers as osolv
+
+from test_oracle_mesh import check_half_edge_invariants
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import paper_2604_06896_gb300 as vx
+    return vx
+
+
+def setup(c):
+    ref = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    return ref, p
+
+
+def gpu_relax(vx, ref, p, dtype, **opts):
+    import torch
+    t = vx.Tissue(ref, dtype)
+    X = torch.tensor(ref["vert"], dtype=torch.float64, device="cuda")
+    r = vx.vx_minimize(t, X, p, **opts)
+    top = t.topology()
+    top["vert"] = X.cpu().numpy()
+    t.close()
+    return r, top
+
+
+def polish(top, p, A0, tol=1e-11):
+    """Oracle FIRE from the GPU state at fixed topology."""
+    o = osolv.MinOpts(tol=tol * np.sqrt(A0), max_iter=200000, dt0=0.01, dt_max=0.5)
+    r = osolv.relax(top["vert"], top, p, o)
+    d = np.sqrt(((r.X - top["vert"]) ** 2).sum(axis=1)).max() / np.sqrt(A0)
+    F = omodel.forces(top["vert"], top, p)
+    return d, np.sqrt((F * F).sum(axis=1)).max(), r
+
+
+@pytest.mark.parametrize("path", ["resident", "plain"])
+def test_c1_fp64_same_trajectory(vx, path):
+    c = vi.tissue_c1()
+    ref, p = setup(c)
+    lmin = 5e-3 * np.sqrt(c["A0"])
+    opts = dict(tol=1e-8, max_iter=20000, dt0=0.01, dt_max=0.5, l_min=lmin)
+    r, top = gpu_relax(vx, ref, p, "f64", path=path, **opts)
+    o = osolv.MinOpts(tol=1e-8, max_iter=20000, dt0=0.01, dt_max=0.5)
+    ro = osolv.relax(ref["vert"], ref, p, o, l_min=lmin)
+    print(f"{path}: gpu iters {r.iters} t1 {r.n_t1} st {r.n_stretch} fmax {r.fmax:.3e}; "
+          f"oracle iters {ro.iters} t1 {ro.n_t1} st {ro.n_stretch}")
+    assert r.converged and r.fmax < 1e-8
+    assert r.path_used == (vx.VX_PATH_RESIDENT if path == "resident" else vx.VX_PATH_PLAIN)
+    check_half_edge_invariants(top)
+    assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
+    assert np.array_equal(top["he"], ro.tissue["he"])
+    assert abs(r.iters - ro.iters) <= 2
+    assert np.abs(top["vert"] - ro.X).max() < 1e-6 * np.sqrt(c["A0"])
+    assert abs(r.energy - omodel.energy(ro.X, ro.tissue, p)) < 1e-9 * abs(r.energy)
+    Fo = omodel.forces(top["vert"], top, p)
+    assert np.sqrt((Fo * Fo).sum(axis=1)).max() < 1e-8
+
+
+@pytest.mark.parametrize("path", ["resident", "plain"])
+def test_fp32_equilibrium_polish(vx, path):
+    c = vi.small_tissue(300, 81, p0=3.7, lam_range=(0.02, 0.1))
+    ref, p = setup(c)
+    r, top = gpu_relax(vx, ref, p, "f32", path=path, tol=1e-6, max_iter=50000, dt0=0.01,
+                       dt_max=0.5, l_min=5e-3)
+    assert r.converged and r.fmax < 1e-6, r
+    check_half_edge_invariants(top)
+    g = omodel.geometry(top["vert"], top)
+    assert abs(g["A"].sum() - c["Lx"] * c["Ly"]) < 1e-9 * c["Lx"] * c["Ly"]
+    d, fo, rp = polish(top, p, c["A0"])
+    print(f"{path}: iters {r.iters} t1 {r.n_t1}; oracle fmax at X_gpu {fo:.2e}; polish moved {d:.2e}")
+    assert rp.converged
+    assert fo < 1e-5
+    assert d < 1e-4
+    E_o = omodel.energy(top["vert"], top, p)
+    assert abs(r.energy - E_o) < 1e-5 * abs(E_o)
+
+
+def test_gd_matches_oracle_steps(vx):
+    """Gradient descent without T1 for a fixed number of steps follows the
+    oracle's iterates (FP64) and lowers the energy."""
+    seeds, Lx, Ly = vi.lattice_seeds(6, 6)
+    ref = omesh.build_periodic_voronoi(seeds, Lx, Ly)
+    A = 1.5 * np.sqrt(3.0) / 3.0
+    p = dict(KA=1.0, KP=1.0, A0=A, P0=3.6 * np.sqrt(A), lam=0.02)
+    ref = dict(ref)
+    ref["vert"] = ref["vert"] + 0.05 * np.random.default_rng(3).standard_normal(ref["vert"].shape)
+    r, top = gpu_relax(vx, ref, p, "f64", method="gd", gd_lr=1e-2, tol=0.0, max_iter=200)
+    ro = osolv.relax(ref["vert"], ref, p, osolv.MinOpts(method="gd", gd_lr=1e-2, tol=0.0, max_iter=200))
+    assert r.iters == 200
+    assert np.abs(top["vert"] - ro.X).max() < 1e-12
+    assert r.energy < omodel.energy(ref["vert"], ref, p)
+
+
+def test_resident_and_plain_agree_fp32(vx):
+    c = vi.small_tissue(200, 82, lam_range=(0.02, 0.1))
+    ref, p = setup(c)
+    kw = dict(tol=1e-6, max_iter=50000, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    r1, t1 = gpu_relax(vx, ref, p, "f32", path="resident", **kw)
+    r2, t2 = gpu_relax(vx, ref, p, "f32", path="plain", **kw)
+    assert r1.converged and r2.converged
+    if np.array_equal(t1["he"], t2["he"]):
+        assert abs(r1.energy - r2.energy) < 1e-5 * abs(r1.energy)
+
+
+def test_not_converged_status(vx):
+    c = vi.small_tissue(50, 83)
+    ref, p = setup(c)
+    r, top = gpu_relax(vx, ref, p, "f32", tol=1e-12, max_iter=10, l_min=5e-3)
+    assert r.status == 1 and r.iters == 10
