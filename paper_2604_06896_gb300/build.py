@@ -2,8 +2,8 @@
 
 Compiles every translation unit under csrc/ in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``) and links them into
-``libvx.so`` next to this file.  Objects go to ``_build/`` at the repository
-root.  A unit is recompiled only when it or a header is newer than its
+``libvx.so`` next to this file.  Objects go to ``_build/<machine>/`` at the
+repository root.  A unit is recompiled only when it or a header is newer than its
 object.
 """
 from __future__ import annotations
@@ -11,6 +11,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -18,7 +19,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(ROOT, "_build")
+BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(PKG, "libvx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
