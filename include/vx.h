@@ -68,7 +68,16 @@ enum { VX_F64 = 0, VX_F32 = 1 };
 enum { VX_FIRE = 0, VX_GD = 1 };
 enum { VX_ADJOINT_CG = 0, VX_EP_CENTERED = 1, VX_EP_FORWARD = 2 };
 enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
-enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2 };
+/* Execution paths of the persistent solvers:
+ *   RESIDENT: one CTA holds the whole tissue in shared memory for the whole
+ *             solve (tissues up to ~1,500 cells in FP32);
+ *   CLUSTER:  a 16-CTA thread-block cluster holds it in L2-resident global
+ *             memory, synchronised by the hardware cluster barrier (up to
+ *             65,536 cells);
+ *   PLAIN:    one kernel launch per sub-step, convergence polled by the
+ *             host every check_every steps (the reference GPU path).
+ *   AUTO picks RESIDENT, then CLUSTER, then PLAIN. */
+enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2, VX_PATH_CLUSTER = 3 };
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* vx_last_error(void);
@@ -118,6 +127,12 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
                            int32_t dtype, void* stream, vx_tissue* out);
 vx_status vx_tissue_destroy(vx_tissue t);
 
+/*
+ * vx_tissue_restore — put back the topology the tissue had at creation
+ * (undoes the T1 transitions of earlier vx_minimize calls).  Asynchronous.
+ */
+vx_status vx_tissue_restore(vx_tissue t, void* stream);
+
 /* Sizes of a tissue: cells, vertices, edges, half-edges. */
 vx_status vx_tissue_sizes(vx_tissue t, int32_t* n_cells, int32_t* n_vertices,
                           int32_t* n_edges, int32_t* n_half_edges);
@@ -150,6 +165,14 @@ typedef struct {
 vx_status vx_energy_forces(vx_tissue t, const double* X, const vx_params* p,
                            double* F, double* E, void* stream);
 
+/*
+ * vx_hessian_vector — Hv = (grad^2_X E) v at X (the operator the adjoint
+ * solves with; Methods, "Implicit differentiation").  X, v, Hv dev float64
+ * [V][2].  Asynchronous on `stream`.
+ */
+vx_status vx_hessian_vector(vx_tissue t, const double* X, const vx_params* p, const double* v,
+                            double* Hv, void* stream);
+
 /* Inner minimiser options (defaults from vx_min_opts_default). */
 typedef struct {
   int32_t method;      /* VX_FIRE or VX_GD                                  */
@@ -161,7 +184,7 @@ typedef struct {
   int32_t n_min;       /* FIRE N_min                                        */
   double  f_inc, f_dec, alpha0, f_alpha;
   double  l_min;       /* T1 threshold; <= 0 disables T1 checks             */
-  int32_t path;        /* VX_PATH_AUTO / RESIDENT / PLAIN                   */
+  int32_t path;        /* VX_PATH_AUTO / RESIDENT / CLUSTER / PLAIN         */
   int32_t check_every; /* PLAIN path: host polls convergence every k steps  */
 } vx_min_opts;
 
@@ -173,7 +196,7 @@ typedef struct {
   int32_t n_inverted;  /* cells with A <= 0 at the end                      */
   double  fmax;        /* max_i |F_i| at the returned X                     */
   double  energy;
-  int32_t path_used;   /* VX_PATH_RESIDENT or VX_PATH_PLAIN                 */
+  int32_t path_used;   /* VX_PATH_RESIDENT, VX_PATH_CLUSTER or VX_PATH_PLAIN */
   int32_t force_evals;
 } vx_min_result;
 

@@ -16,10 +16,11 @@ import numpy as np
 from . import _capi as capi
 from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # noqa: F401
                     VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
-                    VX_PATH_AUTO, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
+                    VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
 
 __all__ = ["vx_build_mesh", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
-           "vx_equilibrium_grad", "Tissue", "EquilibriumFn", "VxError"]
+           "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "Tissue",
+           "EquilibriumFn", "VxError"]
 
 
 def _torch():
@@ -116,7 +117,8 @@ def min_opts(**kw):
         if k == "method" and isinstance(v, str):
             v = {"fire": VX_FIRE, "gd": VX_GD}[v]
         if k == "path" and isinstance(v, str):
-            v = {"auto": VX_PATH_AUTO, "resident": VX_PATH_RESIDENT, "plain": VX_PATH_PLAIN}[v]
+            v = {"auto": VX_PATH_AUTO, "resident": VX_PATH_RESIDENT, "plain": VX_PATH_PLAIN,
+                 "cluster": VX_PATH_CLUSTER}[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown minimiser option {k}")
         setattr(o, k, v)
@@ -167,6 +169,23 @@ class Tissue:
 
 def vx_tissue_create(mesh, dtype="f64"):
     return Tissue(mesh, dtype)
+
+
+def vx_tissue_restore(t: Tissue):
+    """Put back the topology the tissue had at creation (asynchronous)."""
+    capi.check(capi.vx_tissue_restore(t.handle, _stream()), "vx_tissue_restore")
+
+
+def vx_hessian_vector(t: Tissue, X, params, v):
+    """H v at X (device f64 [V,2] tensors)."""
+    torch = _torch()
+    X = _dev_f64(X, (t.V, 2))
+    v = _dev_f64(v, (t.V, 2))
+    prm, keep = make_params(params, t.n, t.E)
+    Hv = torch.empty((t.V, 2), dtype=torch.float64, device="cuda")
+    capi.check(capi.vx_hessian_vector(t.handle, _ptr(X), C.byref(prm), _ptr(v), _ptr(Hv),
+                                      _stream()), "vx_hessian_vector")
+    return Hv
 
 
 def vx_energy_forces(t: Tissue, X, params, forces=True, energy=True):

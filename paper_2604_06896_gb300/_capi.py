@@ -25,7 +25,7 @@ VX_F64, VX_F32 = 0, 1
 VX_FIRE, VX_GD = 0, 1
 VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD = 0, 1, 2
 VX_COST_NONE, VX_COST_V2V, VX_COST_ANISO = 0, 1, 2
-VX_PATH_AUTO, VX_PATH_RESIDENT, VX_PATH_PLAIN = 0, 1, 2
+VX_PATH_AUTO, VX_PATH_RESIDENT, VX_PATH_PLAIN, VX_PATH_CLUSTER = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "VX_OK", 1: "VX_NOT_CONVERGED", 2: "VX_ERR_INVALID_ARG",
                 3: "VX_ERR_DEGENERATE_SEEDS", 4: "VX_ERR_CUDA", 5: "VX_ERR_OOM",
@@ -87,6 +87,9 @@ vx_tissue_destroy = _sig("vx_tissue_destroy", C.c_int, C.c_void_p)
 vx_tissue_sizes = _sig("vx_tissue_sizes", C.c_int, C.c_void_p, P_i32, P_i32, P_i32, P_i32)
 vx_tissue_topology = _sig("vx_tissue_topology", C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_void_p)
+vx_tissue_restore = _sig("vx_tissue_restore", C.c_int, C.c_void_p, C.c_void_p)
+vx_hessian_vector = _sig("vx_hessian_vector", C.c_int, C.c_void_p, C.c_void_p,
+                         C.POINTER(vx_params), C.c_void_p, C.c_void_p, C.c_void_p)
 vx_energy_forces = _sig("vx_energy_forces", C.c_int, C.c_void_p, C.c_void_p,
                         C.POINTER(vx_params), C.c_void_p, C.c_void_p, C.c_void_p)
 vx_min_opts_default = _sig("vx_min_opts_default", None, C.POINTER(vx_min_opts))
@@ -98,7 +101,8 @@ vx_equilibrium_grad = _sig("vx_equilibrium_grad", C.c_int, C.c_void_p, C.c_void_
                            C.c_void_p, C.c_void_p, C.POINTER(vx_grad_result), C.c_void_p)
 
 EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_tissue_create",
-            "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_energy_forces",
+            "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_tissue_restore",
+            "vx_hessian_vector", "vx_energy_forces",
             "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad"]
 
 

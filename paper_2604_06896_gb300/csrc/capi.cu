@@ -218,6 +218,11 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   if (e == cudaSuccess) e = cudaMalloc(&t->touched, bytes(4 * (size_t)(V / 32 + 1)));
   if (e == cudaSuccess) e = cudaMalloc(&t->partE, bytes(3 * 8 * (size_t)nbc));
   if (e == cudaSuccess) e = cudaMalloc(&t->partF, bytes(4 * 8 * (size_t)nbv));
+  if (e == cudaSuccess) e = cudaMalloc(&t->tgt0, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->nxt0, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->face0, bytes(4 * (size_t)HE));
+  if (e == cudaSuccess) e = cudaMalloc(&t->vout0, bytes(12 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->ffirst0, bytes(4 * (size_t)n));
   if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(vx::FireCtrl));
   if (e == cudaSuccess) e = cudaMalloc(&t->dout, sizeof(vx::MinOut));
   t->work = nullptr;
@@ -233,6 +238,11 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   VX_CUDA_TRY(cudaMemcpyAsync(t->face, face.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(t->vout, vout.data(), 12 * (size_t)V, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->tgt0, tgt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->nxt0, nxt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->face0, face.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->vout0, vout.data(), 12 * (size_t)V, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst0, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemsetAsync(t->shortbits, 0, 4 * (size_t)(E / 32 + 1), s));
   VX_CUDA_TRY(cudaMemsetAsync(t->touched, 0, 4 * (size_t)(V / 32 + 1), s));
   VX_CUDA_TRY(cudaStreamSynchronize(s));
@@ -242,13 +252,36 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
 
 vx_status vx_tissue_destroy(vx_tissue t) {
   if (!t) return VX_OK;
-  void* ptrs[] = {t->tgt, t->nxt,       t->face,    t->vout,  t->ffirst, t->Xw,
-                  t->vel, t->F,         t->cellc,   t->shortbits, t->touched, t->partE,
-                  t->partF, t->ctrl,    t->dout,    t->work};
+  void* ptrs[] = {t->tgt,  t->nxt,   t->face,      t->vout,    t->ffirst, t->Xw,
+                  t->vel,  t->F,     t->cellc,     t->shortbits, t->touched, t->partE,
+                  t->partF, t->ctrl, t->dout,      t->work,    t->tgt0,   t->nxt0,
+                  t->face0, t->vout0, t->ffirst0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete t;
   return VX_OK;
+}
+
+vx_status vx_tissue_restore(vx_tissue t, void* stream) {
+  if (!t) return invalid("NULL tissue");
+  cudaStream_t s = as_stream(stream);
+  const size_t HE = t->HE, V = t->V, n = t->n;
+  VX_CUDA_TRY(cudaMemcpyAsync(t->tgt, t->tgt0, 4 * HE, cudaMemcpyDeviceToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->nxt, t->nxt0, 4 * HE, cudaMemcpyDeviceToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->face, t->face0, 4 * HE, cudaMemcpyDeviceToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->vout, t->vout0, 12 * V, cudaMemcpyDeviceToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst, t->ffirst0, 4 * n, cudaMemcpyDeviceToDevice, s));
+  return VX_OK;
+}
+
+vx_status vx_hessian_vector(vx_tissue t, const double* X, const vx_params* p, const double* v,
+                            double* Hv, void* stream) {
+  if (!t || !X || !v || !Hv) return invalid("NULL tissue, X, v or Hv");
+  std::string m;
+  if (!params_ok(p, &m)) return invalid(m);
+  const vx_status s = vx::hessian_vector(t, X, to_params(p), v, Hv, as_stream(stream));
+  if (s != VX_OK) set_error(std::string("vx_hessian_vector: ") + cudaGetErrorString(cudaGetLastError()));
+  return s;
 }
 
 vx_status vx_tissue_sizes(vx_tissue t, int32_t* n_cells, int32_t* n_vertices, int32_t* n_edges,
@@ -336,7 +369,7 @@ static bool min_opts_ok(const vx_min_opts* o, std::string* m) {
   else if (o->max_iter < 0) *m = "max_iter must be >= 0";
   else if (!(o->dt0 > 0) || !(o->dt_max > 0)) *m = "dt0 and dt_max must be positive";
   else if (!(o->gd_lr > 0)) *m = "gd_lr must be positive";
-  else if (o->path < VX_PATH_AUTO || o->path > VX_PATH_PLAIN) *m = "unknown path";
+  else if (o->path < VX_PATH_AUTO || o->path > VX_PATH_CLUSTER) *m = "unknown path";
   else return true;
   return false;
 }
@@ -368,11 +401,7 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
   int used = 0;
   const vx_status s = vx::minimize(t, X, to_params(p), to_min_params(o), o->path, o->check_every,
                                    &out, &used, as_stream(stream));
-  if (s != VX_OK) {
-    if (s == VX_ERR_INVALID_ARG) set_error("the tissue does not fit one CTA's shared memory");
-    else set_error(std::string("vx_minimize: ") + cudaGetErrorString(cudaGetLastError()));
-    return s;
-  }
+  if (s != VX_OK) return s;
   r->status = out.status;
   r->iters = out.iters;
   r->n_t1 = out.n_t1;

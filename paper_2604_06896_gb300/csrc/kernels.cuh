@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "device_math.cuh"
+#include "../../include/vx.h"
 
 namespace vx {
 

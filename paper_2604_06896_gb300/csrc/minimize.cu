@@ -304,300 +304,6 @@ __global__ void k_final_short(View<P> v, double lmin, int* out) {
   *out = c;
 }
 
-// --------------------------------------------------- resident minimiser
-
-struct ResidentArgs {
-  const double* Xin;
-  double* Xout;
-  int n, V, E, HE;
-  double Lx, Ly;
-  // global topology (read at entry, written back at exit)
-  uint32_t* tgt;
-  int32_t *nxt, *face, *vout, *ffirst;
-  ParamsD prm;
-  MinParams mp;
-  MinOut* out;
-};
-
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-template <class P>
-__host__ __device__ inline size_t resident_bytes(int n, int V, int E, int HE, int nthreads) {
-  using R = typename P::R;
-  size_t b = 0;
-  b += align16(sizeof(typename P::Pos) * V);
-  b += align16(sizeof(uint32_t) * HE);
-  b += align16(sizeof(int32_t) * HE);
-  b += align16(sizeof(int32_t) * HE);
-  b += align16(sizeof(int32_t) * 3 * V);
-  b += align16(sizeof(int32_t) * n);
-  b += align16(2 * sizeof(R) * n);
-  b += align16(sizeof(R) * E);
-  b += align16(sizeof(uint32_t) * ((E + 31) / 32));
-  b += align16(sizeof(uint32_t) * ((V + 31) / 32));
-  b += align16(sizeof(double) * 8 * ((nthreads + 31) / 32));
-  return b;
-}
-
-template <class P, int T, int MAXC>
-__global__ void __launch_bounds__(T) k_min_resident(ResidentArgs g) {
-  using R = typename P::R;
-  using Pos = typename P::Pos;
-  using R2 = R2T<R>;
-  constexpr int MAXV = 2 * MAXC;
-  constexpr int NW = T / 32;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int n = g.n, V = g.V, E = g.E, HE = g.HE;
-  unsigned char* p = smem;
-  Pos* sX = (Pos*)p;            p += align16(sizeof(Pos) * V);
-  uint32_t* sTgt = (uint32_t*)p; p += align16(sizeof(uint32_t) * HE);
-  int32_t* sNxt = (int32_t*)p;   p += align16(sizeof(int32_t) * HE);
-  int32_t* sFace = (int32_t*)p;  p += align16(sizeof(int32_t) * HE);
-  int32_t* sVout = (int32_t*)p;  p += align16(sizeof(int32_t) * 3 * V);
-  int32_t* sFf = (int32_t*)p;    p += align16(sizeof(int32_t) * n);
-  R2* sCell = (R2*)p;            p += align16(2 * sizeof(R) * n);
-  R* sLam = (R*)p;               p += align16(sizeof(R) * E);
-  uint32_t* sShort = (uint32_t*)p; p += align16(sizeof(uint32_t) * ((E + 31) / 32));
-  uint32_t* sTouch = (uint32_t*)p; p += align16(sizeof(uint32_t) * ((V + 31) / 32));
-  double* sRed = (double*)p;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-
-  for (int i = tid; i < V; i += T) sX[i] = P::from_d(g.Xin[2 * i], g.Xin[2 * i + 1]);
-  for (int h = tid; h < HE; h += T) {
-    sTgt[h] = g.tgt[h];
-    sNxt[h] = g.nxt[h];
-    sFace[h] = g.face[h];
-  }
-  for (int k = tid; k < 3 * V; k += T) sVout[k] = g.vout[k];
-  for (int c = tid; c < n; c += T) sFf[c] = g.ffirst[c];
-  for (int e = tid; e < E; e += T) sLam[e] = (R)g.prm.la(e);
-  for (int w = tid; w < (E + 31) / 32; w += T) sShort[w] = 0;
-  for (int w = tid; w < (V + 31) / 32; w += T) sTouch[w] = 0;
-
-  View<P> vw;
-  vw.X = sX;
-  vw.tgt = sTgt;
-  vw.nxt = sNxt;
-  vw.face = sFace;
-  vw.vout = sVout;
-  vw.ffirst = sFf;
-  vw.n = n;
-  vw.V = V;
-  vw.E = E;
-  vw.box = P::make_box(g.Lx, g.Ly);
-  vw.Lx = g.Lx;
-  vw.Ly = g.Ly;
-
-  R ka[MAXC], kp[MAXC], a0[MAXC], p0[MAXC];
-#pragma unroll
-  for (int k = 0; k < MAXC; ++k) {
-    const int c = tid + k * T;
-    const int cc = c < n ? c : 0;
-    ka[k] = (R)g.prm.ka(cc);
-    kp[k] = (R)g.prm.kp(cc);
-    a0[k] = (R)g.prm.a0(cc);
-    p0[k] = (R)g.prm.p0(cc);
-  }
-  R vx[MAXV], vy[MAXV], fx[MAXV], fy[MAXV];
-#pragma unroll
-  for (int k = 0; k < MAXV; ++k) vx[k] = vy[k] = fx[k] = fy[k] = 0;
-
-  const MinParams& mp = g.mp;
-  const R lminR = (R)mp.l_min;
-  double dt = mp.dt0, alpha = mp.alpha0;
-  int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
-  double fmx = 0;
-  __syncthreads();
-
-  auto cell_pass = [&](R lm) -> bool {
-    bool fl = false;
-#pragma unroll
-    for (int k = 0; k < MAXC; ++k) {
-      const int c = tid + k * T;
-      if (c < n) {
-        R A, Pp;
-        fl |= cell_geometry(vw, c, A, Pp, lm, sShort);
-        sCell[c] = mk2<R>((R)2 * ka[k] * (A - a0[k]), (R)2 * kp[k] * (Pp - p0[k]));
-      }
-    }
-    return fl;
-  };
-
-  for (it = 0;; ++it) {
-    const bool fl = cell_pass(lminR);
-    if (mp.l_min > 0) {
-      if (__syncthreads_or(fl)) {
-        if (tid == 0) {
-          T1Stats st = {0, 0, 0};
-          int nd = 0;
-          t1_pass(vw, g.prm, mp.l_min, sShort, sTouch, &st, nullptr, 0, &nd);
-          n_t1 += st.n_t1;
-          n_st += st.n_stretch;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < MAXV; ++k) {
-          const int i = tid + k * T;
-          if (i < V && (sTouch[i >> 5] >> (i & 31)) & 1u) vx[k] = vy[k] = 0;
-        }
-        __syncthreads();
-        for (int w = tid; w < (V + 31) / 32; w += T) sTouch[w] = 0;
-        cell_pass((R)0);
-        __syncthreads();
-      }
-    } else {
-      __syncthreads();
-    }
-    // Vertex pass and FIRE reductions.
-    double ff = 0, pv = 0, vv = 0, m2 = 0;
-#pragma unroll
-    for (int k = 0; k < MAXV; ++k) {
-      const int i = tid + k * T;
-      if (i < V) {
-        vertex_force(vw, i, sCell, sLam, 0.0, fx[k], fy[k]);
-        ff += (double)(fx[k] * fx[k] + fy[k] * fy[k]);
-        pv += (double)(fx[k] * vx[k] + fy[k] * vy[k]);
-        vv += (double)(vx[k] * vx[k] + vy[k] * vy[k]);
-        m2 = fmax(m2, (double)(fx[k] * fx[k] + fy[k] * fy[k]));
-      }
-    }
-    ff = warp_sum(ff);
-    pv = warp_sum(pv);
-    vv = warp_sum(vv);
-    m2 = warp_max(m2);
-    if (lane == 0) {
-      sRed[4 * wid] = ff;
-      sRed[4 * wid + 1] = pv;
-      sRed[4 * wid + 2] = vv;
-      sRed[4 * wid + 3] = m2;
-    }
-    __syncthreads();
-    double FF = 0, PW = 0, VVs = 0, M = 0;
-#pragma unroll 4
-    for (int q = 0; q < NW; ++q) {
-      FF += sRed[4 * q];
-      PW += sRed[4 * q + 1];
-      VVs += sRed[4 * q + 2];
-      M = fmax(M, sRed[4 * q + 3]);
-    }
-    fmx = sqrt(M);
-    if (!(fmx == fmx) || isinf(fmx)) {
-      status = VX_ERR_NONFINITE;
-      break;
-    }
-    below = (fmx < mp.tol) ? below + 1 : 0;
-    if (below >= mp.patience) {
-      status = VX_OK;
-      break;
-    }
-    if (it >= mp.max_iter) {
-      status = VX_NOT_CONVERGED;
-      break;
-    }
-    if (mp.method == 1) {
-      const R s = (R)mp.gd_lr;
-#pragma unroll
-      for (int k = 0; k < MAXV; ++k) {
-        const int i = tid + k * T;
-        if (i < V) P::add(sX[i], s * fx[k], s * fy[k]);
-      }
-    } else {
-      R mA = 0, mB = 0;
-      bool zero;
-      if (PW > 0) {
-        mA = (R)(1.0 - alpha);
-        mB = (R)(alpha * sqrt(VVs) / sqrt(FF));
-        zero = false;
-        if (npos > mp.n_min) {
-          dt = fmin(dt * mp.f_inc, mp.dt_max);
-          alpha *= mp.f_alpha;
-        }
-        ++npos;
-      } else {
-        zero = true;
-        dt *= mp.f_dec;
-        alpha = mp.alpha0;
-        npos = 0;
-      }
-      const R dtR = (R)dt;
-#pragma unroll
-      for (int k = 0; k < MAXV; ++k) {
-        const int i = tid + k * T;
-        if (i < V) {
-          R ux = zero ? (R)0 : mA * vx[k] + mB * fx[k];
-          R uy = zero ? (R)0 : mA * vy[k] + mB * fy[k];
-          ux += dtR * fx[k];
-          uy += dtR * fy[k];
-          vx[k] = ux;
-          vy[k] = uy;
-          P::add(sX[i], dtR * ux, dtR * uy);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-
-  // Final energy, inverted cells and short edges at the returned X.
-  double en = 0, inv = 0;
-#pragma unroll
-  for (int k = 0; k < MAXC; ++k) {
-    const int c = tid + k * T;
-    if (c < n) {
-      R A, Pp;
-      double el = 0;
-      cell_geometry(vw, c, A, Pp, (R)0, sShort, &el, &g.prm);
-      const double dA = (double)A - g.prm.a0(c), dP = (double)Pp - g.prm.p0(c);
-      en += g.prm.ka(c) * dA * dA + g.prm.kp(c) * dP * dP + el;
-      inv += (A <= 0) ? 1.0 : 0.0;
-    }
-  }
-  double nsh = 0;
-  if (mp.l_min > 0)
-    for (int e = tid; e < E; e += T) nsh += edge_len_d(vw, 2 * e) < mp.l_min ? 1.0 : 0.0;
-  en = warp_sum(en);
-  inv = warp_sum(inv);
-  nsh = warp_sum(nsh);
-  if (lane == 0) {
-    sRed[4 * wid] = en;
-    sRed[4 * wid + 1] = inv;
-    sRed[4 * wid + 2] = nsh;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double E0 = 0, I0 = 0, S0 = 0;
-    for (int q = 0; q < NW; ++q) {
-      E0 += sRed[4 * q];
-      I0 += sRed[4 * q + 1];
-      S0 += sRed[4 * q + 2];
-    }
-    MinOut o;
-    o.status = status;
-    o.iters = it;
-    o.n_t1 = n_t1;
-    o.n_stretch = n_st;
-    o.n_short = (int)S0;
-    o.n_inverted = (int)I0;
-    o.force_evals = it + 1;
-    o.pad = 0;
-    o.fmax = fmx;
-    o.energy = E0;
-    *g.out = o;
-  }
-  for (int i = tid; i < V; i += T) {
-    const double2 d = P::to_d(sX[i]);
-    g.Xout[2 * i] = d.x;
-    g.Xout[2 * i + 1] = d.y;
-  }
-  for (int h = tid; h < HE; h += T) {
-    g.tgt[h] = sTgt[h];
-    g.nxt[h] = sNxt[h];
-    g.face[h] = sFace[h];
-  }
-  for (int k = tid; k < 3 * V; k += T) g.vout[k] = sVout[k];
-  for (int c = tid; c < n; c += T) g.ffirst[c] = sFf[c];
-}
-
 // ------------------------------------------------------------- host side
 
 static int grid_for(int items, int threads) {
@@ -702,76 +408,14 @@ static vx_status minimize_plain(vx_tissue_s* t, double* X, const ParamsD& prm, c
   return VX_OK;
 }
 
-template <class P, int T, int MAXC>
-static vx_status launch_resident(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
-                                 MinOut* out_h, cudaStream_t s) {
-  const size_t smem = resident_bytes<P>(t->n, t->V, t->E, t->HE, T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_min_resident<P, T, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_set = true;
-  }
-  ResidentArgs a;
-  a.Xin = X;
-  a.Xout = X;
-  a.n = t->n;
-  a.V = t->V;
-  a.E = t->E;
-  a.HE = t->HE;
-  a.Lx = t->Lx;
-  a.Ly = t->Ly;
-  a.tgt = t->tgt;
-  a.nxt = t->nxt;
-  a.face = t->face;
-  a.vout = t->vout;
-  a.ffirst = t->ffirst;
-  a.prm = prm;
-  a.mp = mp;
-  a.out = t->dout;
-  k_min_resident<P, T, MAXC><<<1, T, smem, s>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return VX_ERR_CUDA;
-  if (cudaMemcpyAsync(out_h, t->dout, sizeof(MinOut), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return VX_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return VX_ERR_CUDA;
-  return VX_OK;
-}
-
 template <class P>
-static bool resident_fits(vx_tissue_s* t, int T) {
-  return resident_bytes<P>(t->n, t->V, t->E, t->HE, T) <= 227 * 1024;
+vx_status minimize_plain_t(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
+                           int check_every, MinOut* out_h, cudaStream_t s) {
+  return minimize_plain<P>(t, X, prm, mp, check_every, out_h, s);
 }
-
-template <class P>
-static vx_status minimize_resident(vx_tissue_s* t, double* X, const ParamsD& prm,
-                                   const MinParams& mp, MinOut* out, cudaStream_t s) {
-  // threads per CTA: enough for one cell per thread up to 1024, then 2 / 4
-  const int n = t->n;
-  if (n <= 128) return launch_resident<P, 128, 1>(t, X, prm, mp, out, s);
-  if (n <= 256) return launch_resident<P, 256, 1>(t, X, prm, mp, out, s);
-  if (n <= 512) return launch_resident<P, 512, 1>(t, X, prm, mp, out, s);
-  if (n <= 1024) return launch_resident<P, 1024, 1>(t, X, prm, mp, out, s);
-  if (n <= 2048) return launch_resident<P, 1024, 2>(t, X, prm, mp, out, s);
-  return launch_resident<P, 1024, 4>(t, X, prm, mp, out, s);
-}
-
-vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
-                   int check_every, MinOut* out, int* path_used, cudaStream_t s) {
-  const bool f64 = t->dtype == VX_F64;
-  const bool fits = f64 ? resident_fits<PolF64>(t, 1024) : resident_fits<PolF32>(t, 1024);
-  if (path == VX_PATH_RESIDENT && !fits) return VX_ERR_INVALID_ARG;
-  const bool use_res = (path == VX_PATH_RESIDENT) || (path == VX_PATH_AUTO && fits);
-  *path_used = use_res ? VX_PATH_RESIDENT : VX_PATH_PLAIN;
-  if (use_res)
-    return f64 ? minimize_resident<PolF64>(t, X, prm, mp, out, s)
-               : minimize_resident<PolF32>(t, X, prm, mp, out, s);
-  return f64 ? minimize_plain<PolF64>(t, X, prm, mp, check_every, out, s)
-             : minimize_plain<PolF32>(t, X, prm, mp, check_every, out, s);
-}
-
-size_t resident_smem_bytes(vx_tissue_s* t) {
-  return t->dtype == VX_F64 ? resident_bytes<PolF64>(t->n, t->V, t->E, t->HE, 1024)
-                            : resident_bytes<PolF32>(t->n, t->V, t->E, t->HE, 1024);
-}
+template vx_status minimize_plain_t<PolF64>(vx_tissue_s*, double*, const ParamsD&,
+                                            const MinParams&, int, MinOut*, cudaStream_t);
+template vx_status minimize_plain_t<PolF32>(vx_tissue_s*, double*, const ParamsD&,
+                                            const MinParams&, int, MinOut*, cudaStream_t);
 
 }  // namespace vx

@@ -1,0 +1,389 @@
+// Launchers of the persistent per-tissue kernels: one CTA with the tissue in
+// shared memory ("resident"), or a 16-CTA thread-block cluster with the
+// tissue in L2-resident global memory ("cluster"), for the minimiser and the
+// adjoint; plus the path choice.
+#include <cuda_runtime.h>
+
+#include "persistent.cuh"
+#include "tissue.h"
+#include "vx_internal.h"
+
+namespace vx {
+
+template <class P>
+vx_status minimize_plain_t(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
+                           int check_every, MinOut* out_h, cudaStream_t s);
+
+constexpr int kSmemMax = 227 * 1024;
+constexpr int kClusterT = 1024;
+constexpr int kClusterNR = 16;
+
+__host__ __device__ inline size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared memory of a resident tissue: positions, topology, per-cell
+// coefficients (nc4 = 2 for the minimiser, 4 for the adjoint), tensions,
+// the CG direction (adjoint), bit masks and reduction slots.
+template <class P>
+size_t res_bytes(int n, int V, int E, int HE, int T, bool adjoint) {
+  using R = typename P::R;
+  size_t b = a16(sizeof(typename P::Pos) * V) + 3 * a16(4 * (size_t)HE) + a16(12 * (size_t)V) +
+             a16(4 * (size_t)n) + a16((adjoint ? 4 : 2) * sizeof(R) * n) + a16(sizeof(R) * E) +
+             a16(4 * (size_t)((E + 31) / 32)) + a16(4 * (size_t)((V + 31) / 32)) +
+             3 * a16(8 * 4 * (size_t)(T / 32 + 1));
+  if (adjoint) b += a16(2 * sizeof(R) * V);
+  return b;
+}
+
+struct PersistArgs {
+  const double* Xin;
+  double* Xout;
+  int n, V, E, HE;
+  double Lx, Ly;
+  uint32_t* tgt;
+  int32_t *nxt, *face, *vout, *ffirst;
+  ParamsD prm;
+  MinParams mp;
+  AdjParams ap;
+  MinOut* out;
+  AdjOut* aout;
+  // global workspace (cluster variant)
+  void* Xw;
+  void* cell;
+  void* pvec;
+  uint32_t* shortbits;
+  uint32_t* touched;
+};
+
+template <class P>
+__device__ __forceinline__ View<P> global_view(const PersistArgs& g) {
+  View<P> v;
+  v.X = (typename P::Pos*)g.Xw;
+  v.tgt = g.tgt;
+  v.nxt = g.nxt;
+  v.face = g.face;
+  v.vout = g.vout;
+  v.ffirst = g.ffirst;
+  v.n = g.n;
+  v.V = g.V;
+  v.E = g.E;
+  v.box = P::make_box(g.Lx, g.Ly);
+  v.Lx = g.Lx;
+  v.Ly = g.Ly;
+  return v;
+}
+
+// Copies the tissue into shared memory; returns the view and carves the
+// remaining buffers.
+template <class P, int T>
+__device__ __forceinline__ View<P> load_resident(const PersistArgs& g, unsigned char* smem,
+                                                 bool adjoint, void** cell, void** lamR,
+                                                 void** pvec, uint32_t** sh, uint32_t** tc,
+                                                 Slots* sl) {
+  using R = typename P::R;
+  using Pos = typename P::Pos;
+  const int n = g.n, V = g.V, E = g.E, HE = g.HE, tid = threadIdx.x;
+  unsigned char* p = smem;
+  Pos* sX = (Pos*)p;             p += a16(sizeof(Pos) * V);
+  uint32_t* sTgt = (uint32_t*)p; p += a16(4 * (size_t)HE);
+  int32_t* sNxt = (int32_t*)p;   p += a16(4 * (size_t)HE);
+  int32_t* sFace = (int32_t*)p;  p += a16(4 * (size_t)HE);
+  int32_t* sVout = (int32_t*)p;  p += a16(12 * (size_t)V);
+  int32_t* sFf = (int32_t*)p;    p += a16(4 * (size_t)n);
+  *cell = p;                     p += a16((adjoint ? 4 : 2) * sizeof(R) * n);
+  R* sLam = (R*)p;               p += a16(sizeof(R) * E);
+  *sh = (uint32_t*)p;            p += a16(4 * (size_t)((E + 31) / 32));
+  *tc = (uint32_t*)p;            p += a16(4 * (size_t)((V + 31) / 32));
+  const size_t sb = a16(8 * 4 * (size_t)(T / 32 + 1));
+  sl->a = (double*)p;            p += sb;
+  sl->b = (double*)p;            p += sb;
+  sl->c = (double*)p;            p += sb;
+  if (adjoint) *pvec = p;
+  for (int h = tid; h < HE; h += T) {
+    sTgt[h] = g.tgt[h];
+    sNxt[h] = g.nxt[h];
+    sFace[h] = g.face[h];
+  }
+  for (int k = tid; k < 3 * V; k += T) sVout[k] = g.vout[k];
+  for (int c = tid; c < n; c += T) sFf[c] = g.ffirst[c];
+  for (int e = tid; e < E; e += T) sLam[e] = (R)g.prm.la(e);
+  for (int w = tid; w < (E + 31) / 32; w += T) (*sh)[w] = 0;
+  for (int w = tid; w < (V + 31) / 32; w += T) (*tc)[w] = 0;
+  *lamR = sLam;
+  View<P> v;
+  v.X = sX;
+  v.tgt = sTgt;
+  v.nxt = sNxt;
+  v.face = sFace;
+  v.vout = sVout;
+  v.ffirst = sFf;
+  v.n = n;
+  v.V = V;
+  v.E = E;
+  v.box = P::make_box(g.Lx, g.Ly);
+  v.Lx = g.Lx;
+  v.Ly = g.Ly;
+  return v;
+}
+
+template <class P, int T>
+__device__ __forceinline__ void store_topology(const PersistArgs& g, const View<P>& v) {
+  const int tid = threadIdx.x;
+  for (int h = tid; h < g.HE; h += T) {
+    g.tgt[h] = v.tgt[h];
+    g.nxt[h] = v.nxt[h];
+    g.face[h] = v.face[h];
+  }
+  for (int k = tid; k < 3 * g.V; k += T) g.vout[k] = v.vout[k];
+  for (int c = tid; c < g.n; c += T) g.ffirst[c] = v.ffirst[c];
+}
+
+template <class P, int T, int MAXC>
+__global__ void __launch_bounds__(T) k_min_res(PersistArgs g) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  void *cell, *lam, *pvec;
+  uint32_t *sh, *tc;
+  Slots sl;
+  View<P> v = load_resident<P, T>(g, smem, false, &cell, &lam, &pvec, &sh, &tc, &sl);
+  __syncthreads();
+  BlockTeam<T> tm;
+  min_body<P, BlockTeam<T>, MAXC>(tm, v, (R2*)cell, (const typename P::R*)lam, sh, tc, sl, g.prm,
+                                  g.mp, g.Xin, g.Xout, g.out);
+  __syncthreads();
+  store_topology<P, T>(g, v);
+}
+
+template <class P, int T, int MAXC>
+__global__ void __launch_bounds__(T) k_adj_res(PersistArgs g) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  using R4 = typename Vec2Of<typename P::R>::T4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  void *cell, *lam, *pvec;
+  uint32_t *sh, *tc;
+  Slots sl;
+  View<P> v = load_resident<P, T>(g, smem, true, &cell, &lam, &pvec, &sh, &tc, &sl);
+  __syncthreads();
+  BlockTeam<T> tm;
+  adj_body<P, BlockTeam<T>, MAXC>(tm, v, (R4*)cell, (const typename P::R*)lam, (R2*)pvec, sl,
+                                  g.prm, g.ap, g.Xin, g.aout);
+}
+
+template <class P, int T, int NR, int MAXC>
+__global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  __shared__ double slots[3][4 * (T / 32 + 1)];
+  ClusterTeam<T, NR> tm;
+  for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
+  for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
+  Slots sl = {slots[0], slots[1], slots[2]};
+  min_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
+                                        g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
+  tm.sync();
+}
+
+template <class P, int T, int NR, int MAXC>
+__global__ void __launch_bounds__(T) k_adj_cluster(PersistArgs g) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  using R4 = typename Vec2Of<typename P::R>::T4;
+  __shared__ double slots[3][4 * (T / 32 + 1)];
+  ClusterTeam<T, NR> tm;
+  Slots sl = {slots[0], slots[1], slots[2]};
+  adj_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R4*)g.cell, g.prm.lam,
+                                        (R2*)g.pvec, sl, g.prm, g.ap, g.Xin, g.aout);
+  tm.sync();
+}
+
+// ------------------------------------------------------------------ host
+
+static PersistArgs make_args(vx_tissue_s* t, const double* Xin, double* Xout, const ParamsD& prm) {
+  PersistArgs a = {};
+  a.Xin = Xin;
+  a.Xout = Xout;
+  a.n = t->n;
+  a.V = t->V;
+  a.E = t->E;
+  a.HE = t->HE;
+  a.Lx = t->Lx;
+  a.Ly = t->Ly;
+  a.tgt = t->tgt;
+  a.nxt = t->nxt;
+  a.face = t->face;
+  a.vout = t->vout;
+  a.ffirst = t->ffirst;
+  a.prm = prm;
+  a.out = t->dout;
+  a.aout = (AdjOut*)t->dout;
+  a.Xw = t->Xw;
+  a.cell = t->cellc;
+  a.pvec = t->vel;
+  a.shortbits = t->shortbits;
+  a.touched = t->touched;
+  return a;
+}
+
+template <class K>
+static cudaError_t launch_res(K kernel, int T, size_t smem, const PersistArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+  if (e != cudaSuccess) return e;
+  kernel<<<1, T, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P, bool ADJ>
+static cudaError_t dispatch_res(vx_tissue_s* t, const PersistArgs& a, cudaStream_t s) {
+  const int n = t->n;
+  int T;
+  if (n <= 128) T = 128;
+  else if (n <= 256) T = 256;
+  else if (n <= 512) T = 512;
+  else T = 1024;
+  const size_t smem = res_bytes<P>(t->n, t->V, t->E, t->HE, T, ADJ);
+  if (ADJ) {
+    if (T == 128) return launch_res(k_adj_res<P, 128, 1>, T, smem, a, s);
+    if (T == 256) return launch_res(k_adj_res<P, 256, 1>, T, smem, a, s);
+    if (T == 512) return launch_res(k_adj_res<P, 512, 1>, T, smem, a, s);
+    if (n <= 1024) return launch_res(k_adj_res<P, 1024, 1>, T, smem, a, s);
+    return launch_res(k_adj_res<P, 1024, 2>, T, smem, a, s);
+  }
+  if (T == 128) return launch_res(k_min_res<P, 128, 1>, T, smem, a, s);
+  if (T == 256) return launch_res(k_min_res<P, 256, 1>, T, smem, a, s);
+  if (T == 512) return launch_res(k_min_res<P, 512, 1>, T, smem, a, s);
+  if (n <= 1024) return launch_res(k_min_res<P, 1024, 1>, T, smem, a, s);
+  return launch_res(k_min_res<P, 1024, 2>, T, smem, a, s);
+}
+
+template <class K>
+static cudaError_t launch_cluster(K kernel, const PersistArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterNR, 1, 1);
+  cfg.blockDim = dim3(kClusterT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterNR;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorInvalidConfiguration;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+template <class P, bool ADJ>
+static cudaError_t dispatch_cluster(vx_tissue_s* t, const PersistArgs& a, cudaStream_t s) {
+  const int per = kClusterT * kClusterNR;
+  if (ADJ) {
+    if (t->n <= per) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 1>, a, s);
+    if (t->n <= 2 * per) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+    return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 4>, a, s);
+  }
+  if (t->n <= per) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 1>, a, s);
+  if (t->n <= 2 * per) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+  return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 4>, a, s);
+}
+
+bool resident_fits(vx_tissue_s* t, bool adjoint) {
+  const size_t b = t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, 1024, adjoint)
+                                      : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, 1024, adjoint);
+  return b <= (size_t)kSmemMax && t->n <= 2048;
+}
+
+bool cluster_fits(vx_tissue_s* t) { return t->n <= 4 * kClusterT * kClusterNR; }
+
+size_t resident_smem_bytes(vx_tissue_s* t) {
+  return t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, 1024, false)
+                            : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, 1024, false);
+}
+
+static int choose_path(vx_tissue_s* t, int path, bool adjoint) {
+  if (path == VX_PATH_AUTO) {
+    if (resident_fits(t, adjoint)) return VX_PATH_RESIDENT;
+    if (cluster_fits(t)) return VX_PATH_CLUSTER;
+    return adjoint ? -1 : VX_PATH_PLAIN;
+  }
+  if (path == VX_PATH_RESIDENT && !resident_fits(t, adjoint)) return -1;
+  if (path == VX_PATH_CLUSTER && !cluster_fits(t)) return -1;
+  if (path == VX_PATH_PLAIN && adjoint) return VX_PATH_CLUSTER;
+  return path;
+}
+
+vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
+                   int check_every, MinOut* out, int* path_used, cudaStream_t s) {
+  const int p = choose_path(t, path, false);
+  if (p < 0) {
+    set_error("the requested path cannot hold this tissue");
+    return VX_ERR_INVALID_ARG;
+  }
+  *path_used = p;
+  const bool f64 = t->dtype == VX_F64;
+  if (p == VX_PATH_PLAIN)
+    return f64 ? minimize_plain_t<PolF64>(t, X, prm, mp, check_every, out, s)
+               : minimize_plain_t<PolF32>(t, X, prm, mp, check_every, out, s);
+  PersistArgs a = make_args(t, X, X, prm);
+  a.mp = mp;
+  cudaError_t e;
+  if (p == VX_PATH_RESIDENT)
+    e = f64 ? dispatch_res<PolF64, false>(t, a, s) : dispatch_res<PolF32, false>(t, a, s);
+  else
+    e = f64 ? dispatch_cluster<PolF64, false>(t, a, s) : dispatch_cluster<PolF32, false>(t, a, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("persistent minimiser launch: ") + cudaGetErrorString(e));
+    return VX_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(out, t->dout, sizeof(MinOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error(std::string("vx_minimize: ") + cudaGetErrorString(cudaGetLastError()));
+    return VX_ERR_CUDA;
+  }
+  return VX_OK;
+}
+
+vx_status adjoint_solve(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
+                        int path, AdjOut* out, cudaStream_t s) {
+  const int p = choose_path(t, path, true);
+  if (p < 0) {
+    set_error("the tissue is too large for the adjoint kernels");
+    return VX_ERR_INVALID_ARG;
+  }
+  PersistArgs a = make_args(t, Xstar, nullptr, prm);
+  a.ap = ap;
+  if (p == VX_PATH_CLUSTER) {
+    // per-cell 4-vectors in the workspace
+    const size_t need = 4 * (size_t)t->n + 64;
+    if (t->work_doubles < need + 4 * (size_t)t->V) {
+      if (t->work) cudaFree(t->work);
+      t->work = nullptr;
+      t->work_doubles = 0;
+      if (cudaMalloc(&t->work, 8 * (need + 4 * (size_t)t->V)) != cudaSuccess) {
+        set_error("out of device memory for the adjoint workspace");
+        return VX_ERR_OOM;
+      }
+      t->work_doubles = need + 4 * (size_t)t->V;
+    }
+    a.cell = t->work;
+  }
+  const bool f64 = t->dtype == VX_F64;
+  cudaError_t e;
+  if (p == VX_PATH_RESIDENT)
+    e = f64 ? dispatch_res<PolF64, true>(t, a, s) : dispatch_res<PolF32, true>(t, a, s);
+  else
+    e = f64 ? dispatch_cluster<PolF64, true>(t, a, s) : dispatch_cluster<PolF32, true>(t, a, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("adjoint launch: ") + cudaGetErrorString(e));
+    return VX_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(out, t->dout, sizeof(AdjOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error(std::string("adjoint: ") + cudaGetErrorString(cudaGetLastError()));
+    return VX_ERR_CUDA;
+  }
+  return VX_OK;
+}
+
+}  // namespace vx

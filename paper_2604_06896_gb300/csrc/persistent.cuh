@@ -1,0 +1,631 @@
+// Persistent per-tissue bodies, written once for any Team (team.cuh):
+//   min_body  - the whole FIRE / GD loop with T1 checks (Methods,
+//               "Simulation engine", "T1 transitions"), optionally nudged by
+//               -s Pi grad_X C (a phase of equilibrium propagation);
+//   adj_body  - the implicit adjoint (Methods, "Implicit differentiation"):
+//               preconditioned CG for H lam = Pi grad_X C on a Hessian-vector
+//               product, then g = -(d^2E / dX dtheta)^T lam.
+// Per-item state (velocities, forces, CG vectors) lives in registers of the
+// thread that owns the item; positions, topology, cell coefficients and the
+// CG direction live wherever the View points (shared memory for a resident
+// CTA, L2-resident global memory for a cluster).
+#pragma once
+#include "device_math.cuh"
+#include "kernels.cuh"
+#include "team.cuh"
+
+namespace vx {
+
+template <class R>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> {
+  using T = float2;
+  using T4 = float4;
+};
+template <>
+struct Vec2Of<double> {
+  using T = double2;
+  using T4 = double4;
+};
+
+// Slots for team reductions: three independent banks (each used at most once
+// between two team barriers).
+struct Slots {
+  double* a;
+  double* b;
+  double* c;
+};
+
+// Minimum-image v2v cost gradient at vertex i: (x_i - x_target,i) / N.
+template <class P>
+__device__ __forceinline__ void v2v_grad(const View<P>& v, int i, const double* Xt, double& gx,
+                                         double& gy) {
+  const double2 x = P::to_d(v.X[i]);
+  double dx = x.x - Xt[2 * i], dy = x.y - Xt[2 * i + 1];
+  dx -= v.Lx * rint(dx / v.Lx);
+  dy -= v.Ly * rint(dy / v.Ly);
+  gx = dx / v.V;
+  gy = dy / v.V;
+}
+
+// --------------------------------------------------------------- minimiser
+
+template <class P, class Team, int MAXC, class LamT>
+__device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P::R>::T* cell,
+                         const LamT* lam, uint32_t* shortbits, uint32_t* touched, Slots sl,
+                         const ParamsD& prm, const MinParams& mp, const double* Xin,
+                         double* Xout, MinOut* out) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  constexpr int MAXV = 2 * MAXC;
+  const int n = vw.n, V = vw.V, E = vw.E;
+  const int f0 = tm.first(), st = tm.stride();
+
+  // Positions in (the owner converts), registers for per-item state.
+  if (Xin)
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      if (i < V) vw.X[i] = P::from_d(Xin[2 * i], Xin[2 * i + 1]);
+    }
+  R ka[MAXC], kp[MAXC], a0[MAXC], p0[MAXC];
+#pragma unroll
+  for (int k = 0; k < MAXC; ++k) {
+    const int c = f0 + k * st;
+    const int cc = c < n ? c : 0;
+    ka[k] = (R)prm.ka(cc);
+    kp[k] = (R)prm.kp(cc);
+    a0[k] = (R)prm.a0(cc);
+    p0[k] = (R)prm.p0(cc);
+  }
+  R vx[MAXV], vy[MAXV], fx[MAXV], fy[MAXV];
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) vx[k] = vy[k] = fx[k] = fy[k] = 0;
+  tm.sync();
+
+  // Nudged phase: -s Pi grad C, with the mean of grad C taken once (the
+  // centroid is conserved because every force term sums to zero).
+  double nmx = 0, nmy = 0;
+  const bool nudged = mp.cost == 1 && mp.nudge_s != 0.0;
+  if (nudged) {
+    double s2[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      if (i < V) {
+        double gx, gy;
+        v2v_grad(vw, i, mp.cost_data, gx, gy);
+        s2[0] += gx;
+        s2[1] += gy;
+      }
+    }
+    tm.template reduce<2>(s2, sl.c, 0);
+    nmx = s2[0] / V;
+    nmy = s2[1] / V;
+  }
+
+  const R lminR = (R)mp.l_min;
+  double dt = mp.dt0, alpha = mp.alpha0, fmx = 0;
+  int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
+
+  auto cell_pass = [&](R lm) -> bool {
+    bool fl = false;
+#pragma unroll
+    for (int k = 0; k < MAXC; ++k) {
+      const int c = f0 + k * st;
+      if (c < n) {
+        R A, Pp;
+        fl |= cell_geometry(vw, c, A, Pp, lm, shortbits);
+        R2 cc;
+        cc.x = (R)2 * ka[k] * (A - a0[k]);
+        cc.y = (R)2 * kp[k] * (Pp - p0[k]);
+        cell[c] = cc;
+      }
+    }
+    return fl;
+  };
+
+  for (it = 0;; ++it) {
+    const bool fl = cell_pass(lminR);
+    if (mp.l_min > 0) {
+      if (tm.sync_or(fl, sl.b)) {
+        if (tm.leader()) {
+          T1Stats s1 = {0, 0, 0};
+          int nd = 0;
+          t1_pass(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, &nd);
+          n_t1 += s1.n_t1;
+          n_st += s1.n_stretch;
+        }
+        tm.sync();
+#pragma unroll
+        for (int k = 0; k < MAXV; ++k) {
+          const int i = f0 + k * st;
+          if (i < V && ((touched[i >> 5] >> (i & 31)) & 1u)) vx[k] = vy[k] = 0;
+        }
+        tm.sync();
+        for (int w = f0; w < (V + 31) / 32; w += st) touched[w] = 0;
+        cell_pass((R)0);
+        tm.sync();
+      }
+    } else {
+      tm.sync();
+    }
+    double red[4] = {0, 0, 0, 0};  // F.F, F.v, v.v, max |F_i|^2
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      if (i < V) {
+        vertex_force(vw, i, cell, lam, prm.lam_s, fx[k], fy[k]);
+        if (nudged) {
+          double gx, gy;
+          v2v_grad(vw, i, mp.cost_data, gx, gy);
+          fx[k] -= (R)(mp.nudge_s * (gx - nmx));
+          fy[k] -= (R)(mp.nudge_s * (gy - nmy));
+        }
+        const double f2 = (double)(fx[k] * fx[k] + fy[k] * fy[k]);
+        red[0] += f2;
+        red[1] += (double)(fx[k] * vx[k] + fy[k] * vy[k]);
+        red[2] += (double)(vx[k] * vx[k] + vy[k] * vy[k]);
+        red[3] = fmax(red[3], f2);
+      }
+    }
+    tm.template reduce<4>(red, sl.a, 1);
+    fmx = sqrt(red[3]);
+    if (!(fmx == fmx) || isinf(fmx)) {
+      status = VX_ERR_NONFINITE;
+      break;
+    }
+    below = (fmx < mp.tol) ? below + 1 : 0;
+    if (below >= mp.patience) {
+      status = VX_OK;
+      break;
+    }
+    if (it >= mp.max_iter) {
+      status = VX_NOT_CONVERGED;
+      break;
+    }
+    if (mp.method == 1) {
+      const R s = (R)mp.gd_lr;
+#pragma unroll
+      for (int k = 0; k < MAXV; ++k) {
+        const int i = f0 + k * st;
+        if (i < V) P::add(vw.X[i], s * fx[k], s * fy[k]);
+      }
+    } else {
+      R mA = 0, mB = 0;
+      bool zero;
+      if (red[1] > 0) {
+        mA = (R)(1.0 - alpha);
+        mB = (R)(alpha * sqrt(red[2]) / sqrt(red[0]));
+        zero = false;
+        if (npos > mp.n_min) {
+          dt = fmin(dt * mp.f_inc, mp.dt_max);
+          alpha *= mp.f_alpha;
+        }
+        ++npos;
+      } else {
+        zero = true;
+        dt *= mp.f_dec;
+        alpha = mp.alpha0;
+        npos = 0;
+      }
+      const R dtR = (R)dt;
+#pragma unroll
+      for (int k = 0; k < MAXV; ++k) {
+        const int i = f0 + k * st;
+        if (i < V) {
+          R ux = zero ? (R)0 : mA * vx[k] + mB * fx[k];
+          R uy = zero ? (R)0 : mA * vy[k] + mB * fy[k];
+          ux += dtR * fx[k];
+          uy += dtR * fy[k];
+          vx[k] = ux;
+          vy[k] = uy;
+          P::add(vw.X[i], dtR * ux, dtR * uy);
+        }
+      }
+    }
+    tm.sync();
+  }
+  tm.sync();
+
+  // Energy, inverted cells and short edges at the returned X.
+  double fin[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < MAXC; ++k) {
+    const int c = f0 + k * st;
+    if (c < n) {
+      R A, Pp;
+      double el = 0;
+      cell_geometry(vw, c, A, Pp, (R)0, shortbits, &el, &prm);
+      const double dA = (double)A - prm.a0(c), dP = (double)Pp - prm.p0(c);
+      fin[0] += prm.ka(c) * dA * dA + prm.kp(c) * dP * dP + el;
+      fin[1] += (A <= 0) ? 1.0 : 0.0;
+    }
+  }
+  if (mp.l_min > 0)
+    for (int e = f0; e < E; e += st) fin[2] += edge_len_d(vw, 2 * e) < mp.l_min ? 1.0 : 0.0;
+  tm.template reduce<3>(fin, sl.c, 0);
+  if (tm.leader() && out) {
+    MinOut o;
+    o.status = status;
+    o.iters = it;
+    o.n_t1 = n_t1;
+    o.n_stretch = n_st;
+    o.n_short = (int)fin[2];
+    o.n_inverted = (int)fin[1];
+    o.force_evals = it + 1;
+    o.pad = 0;
+    o.fmax = fmx;
+    o.energy = fin[0];
+    *out = o;
+  }
+  if (Xout)
+    for (int i = f0; i < V; i += st) {
+      const double2 d = P::to_d(vw.X[i]);
+      Xout[2 * i] = d.x;
+      Xout[2 * i + 1] = d.y;
+    }
+}
+
+// ----------------------------------------------------------------- adjoint
+
+struct AdjParams {
+  const double* dCdX;   // [V][2] or null (then the built-in cost)
+  int cost;             // 1 v2v
+  const double* cost_data;
+  double rtol;
+  int max_iter;
+  double* g_lam;        // [E] or null
+  double* g_A0;         // [n] or null
+  double* g_P0;         // [n] or null
+};
+
+struct AdjOut {
+  int status, iters;
+  double rel_residual, cost;
+};
+
+// Directional derivatives of one cell's area and perimeter along `vec`:
+// sA = grad A . vec = 1/2 sum [cross(q_k, w_{k+1}) + cross(w_k, q_{k+1})],
+// sP = grad P . vec = sum u_k . (w_{k+1} - w_k).
+template <class P, class VT>
+__device__ __forceinline__ void cell_dir(const View<P>& v, int c, const VT* vec,
+                                         typename P::R& sA, typename P::R& sP) {
+  using R = typename P::R;
+  const int h0 = v.ffirst[c];
+  const int v0 = src_of(v, h0);
+  const typename P::Pos X0 = v.X[v0];
+  VT w = vec[v0];
+  R qx = 0, qy = 0, a = 0, pp = 0;
+  int cx = 0, cy = 0, h = h0, guard = 0;
+  do {
+    const uint32_t tg = v.tgt[h];
+    cx += tgt_ox(tg);
+    cy += tgt_oy(tg);
+    R nx, ny;
+    const int j = tgt_v(tg);
+    P::diff(v.X[j], X0, cx, cy, v.box, nx, ny);
+    const VT wn = vec[j];
+    a += qx * (R)wn.y - qy * (R)wn.x + (R)w.x * ny - (R)w.y * nx;
+    const R ex = nx - qx, ey = ny - qy;
+    const R rl = P::rsqrt(ex * ex + ey * ey);
+    pp += (ex * ((R)wn.x - (R)w.x) + ey * ((R)wn.y - (R)w.y)) * rl;
+    qx = nx;
+    qy = ny;
+    w = wn;
+    h = v.nxt[h];
+  } while (h != h0 && ++guard < 4096);
+  sA = (R)0.5 * a;
+  sP = pp;
+}
+
+// (H vec)_i, with per cell (cA, cP, 2 K_A sA, 2 K_P sP) in cell4.
+template <class P, class C4, class LamT, class VT>
+__device__ __forceinline__ void vertex_hvp(const View<P>& v, int i, const C4* cell4,
+                                           const LamT* lam, double lam_s, const VT* vec,
+                                           typename P::R& hx, typename P::R& hy) {
+  using R = typename P::R;
+  const typename P::Pos Xi = v.X[i];
+  const VT vi = vec[i];
+  R dx[3], dy[3], ux[3], uy[3], il[3], cA[3], cP[3], zA[3], zP[3], la[3], wx[3], wy[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int h = v.vout[a * v.V + i];
+    const uint32_t tg = v.tgt[h];
+    const int j = tgt_v(tg);
+    P::diff(v.X[j], Xi, tgt_ox(tg), tgt_oy(tg), v.box, dx[a], dy[a]);
+    il[a] = P::rsqrt(dx[a] * dx[a] + dy[a] * dy[a]);
+    ux[a] = dx[a] * il[a];
+    uy[a] = dy[a] * il[a];
+    const C4 cc = cell4[v.face[h]];
+    cA[a] = (R)cc.x;
+    cP[a] = (R)cc.y;
+    zA[a] = (R)cc.z;
+    zP[a] = (R)cc.w;
+    la[a] = lam ? (R)lam[h >> 1] : (R)lam_s;
+    const VT wj = vec[j];
+    wx[a] = (R)wj.x;
+    wy[a] = (R)wj.y;
+  }
+  R gx = 0, gy = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int am = (a + 2) % 3, ap = (a + 1) % 3;
+    const R T = la[a] + cP[a] + cP[am];
+    // T M_a (v_i - w_a), M = (I - u u^T) / l
+    const R ex = (R)vi.x - wx[a], ey = (R)vi.y - wy[a];
+    const R ue = ux[a] * ex + uy[a] * ey;
+    gx += T * il[a] * (ex - ue * ux[a]);
+    gy += T * il[a] * (ey - ue * uy[a]);
+    // 2 K_A sA grad_i A = zA * 1/2 rot(d_a - d_{a+1})
+    gx += (R)0.5 * zA[a] * (dy[a] - dy[ap]);
+    gy -= (R)0.5 * zA[a] * (dx[a] - dx[ap]);
+    // 2 K_A (A - A0) (grad^2 A vec)_i = cA * 1/2 rot(w_a - w_{a+1})
+    gx += (R)0.5 * cA[a] * (wy[a] - wy[ap]);
+    gy -= (R)0.5 * cA[a] * (wx[a] - wx[ap]);
+    // 2 K_P sP grad_i P = zP * (-u_a - u_{a+1})
+    gx -= zP[a] * (ux[a] + ux[ap]);
+    gy -= zP[a] * (uy[a] + uy[ap]);
+  }
+  hx = gx;
+  hy = gy;
+}
+
+// 2 x 2 diagonal block of H at vertex i (K2A, K2P = 2 K_A, 2 K_P per cell in
+// cell4.z / .w): sum_a T_a M_a + 2 K_A gA gA^T + 2 K_P gP gP^T.
+template <class P, class C4, class LamT>
+__device__ __forceinline__ void vertex_diag(const View<P>& v, int i, const C4* cell4,
+                                            const LamT* lam, double lam_s, double& dxx,
+                                            double& dxy, double& dyy) {
+  using R = typename P::R;
+  const typename P::Pos Xi = v.X[i];
+  double dx[3], dy[3], ux[3], uy[3], il[3], cP[3], kA[3], kP[3], la[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int h = v.vout[a * v.V + i];
+    const uint32_t tg = v.tgt[h];
+    R ddx, ddy;
+    P::diff(v.X[tgt_v(tg)], Xi, tgt_ox(tg), tgt_oy(tg), v.box, ddx, ddy);
+    dx[a] = ddx;
+    dy[a] = ddy;
+    il[a] = 1.0 / sqrt(dx[a] * dx[a] + dy[a] * dy[a]);
+    ux[a] = dx[a] * il[a];
+    uy[a] = dy[a] * il[a];
+    const C4 cc = cell4[v.face[h]];
+    cP[a] = (double)cc.y;
+    kA[a] = (double)cc.z;
+    kP[a] = (double)cc.w;
+    la[a] = lam ? (double)lam[h >> 1] : lam_s;
+  }
+  dxx = dxy = dyy = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int am = (a + 2) % 3, ap = (a + 1) % 3;
+    const double T = la[a] + cP[a] + cP[am];
+    dxx += T * il[a] * (1.0 - ux[a] * ux[a]);
+    dxy += T * il[a] * (-ux[a] * uy[a]);
+    dyy += T * il[a] * (1.0 - uy[a] * uy[a]);
+    const double gAx = 0.5 * (dy[a] - dy[ap]), gAy = -0.5 * (dx[a] - dx[ap]);
+    const double gPx = -(ux[a] + ux[ap]), gPy = -(uy[a] + uy[ap]);
+    dxx += kA[a] * gAx * gAx + kP[a] * gPx * gPx;
+    dxy += kA[a] * gAx * gAy + kP[a] * gPx * gPy;
+    dyy += kA[a] * gAy * gAy + kP[a] * gPy * gPy;
+  }
+}
+
+template <class P, class Team, int MAXC, class LamT>
+__device__ void adj_body(const Team& tm, View<P> vw, typename Vec2Of<typename P::R>::T4* cell4,
+                         const LamT* lam, typename Vec2Of<typename P::R>::T* pvec, Slots sl,
+                         const ParamsD& prm, const AdjParams& ap, const double* Xin,
+                         AdjOut* out) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  using R4 = typename Vec2Of<R>::T4;
+  constexpr int MAXV = 2 * MAXC;
+  const int n = vw.n, V = vw.V, E = vw.E;
+  const int f0 = tm.first(), st = tm.stride();
+
+  if (Xin)
+    for (int i = f0; i < V; i += st) vw.X[i] = P::from_d(Xin[2 * i], Xin[2 * i + 1]);
+  R k2a[MAXC], k2p[MAXC];
+#pragma unroll
+  for (int k = 0; k < MAXC; ++k) {
+    const int c = f0 + k * st;
+    const int cc = c < n ? c : 0;
+    k2a[k] = (R)(2.0 * prm.ka(cc));
+    k2p[k] = (R)(2.0 * prm.kp(cc));
+  }
+  tm.sync();
+  // Forward geometry at X*: (cA, cP, 2 K_A, 2 K_P) per cell.
+#pragma unroll
+  for (int k = 0; k < MAXC; ++k) {
+    const int c = f0 + k * st;
+    if (c < n) {
+      R A, Pp;
+      cell_geometry(vw, c, A, Pp, (R)0, nullptr);
+      R4 q;
+      q.x = (R)(2.0 * prm.ka(c) * ((double)A - prm.a0(c)));
+      q.y = (R)(2.0 * prm.kp(c) * ((double)Pp - prm.p0(c)));
+      q.z = k2a[k];
+      q.w = k2p[k];
+      cell4[c] = q;
+    }
+  }
+  tm.sync();
+  // Preconditioner (inverse of the 2 x 2 diagonal blocks) and right side.
+  R ia[MAXV], ib[MAXV], ic[MAXV], rx[MAXV], ry[MAXV], lx[MAXV], ly[MAXV];
+  double s3[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) {
+    const int i = f0 + k * st;
+    rx[k] = ry[k] = lx[k] = ly[k] = 0;
+    ia[k] = ic[k] = 1;
+    ib[k] = 0;
+    if (i < V) {
+      double dxx, dxy, dyy;
+      vertex_diag(vw, i, cell4, lam, prm.lam_s, dxx, dxy, dyy);
+      const double det = dxx * dyy - dxy * dxy;
+      if (dxx > 0 && det > 1e-300 * dxx * dxx) {
+        ia[k] = (R)(dyy / det);
+        ib[k] = (R)(-dxy / det);
+        ic[k] = (R)(dxx / det);
+      } else {
+        const double tr = fabs(dxx) + fabs(dyy);
+        ia[k] = ic[k] = (R)(tr > 0 ? 2.0 / tr : 1.0);
+      }
+      double gx, gy;
+      if (ap.dCdX) {
+        gx = ap.dCdX[2 * i];
+        gy = ap.dCdX[2 * i + 1];
+      } else {
+        v2v_grad(vw, i, ap.cost_data, gx, gy);
+        s3[2] += 0.5 * V * (gx * gx + gy * gy);  // C = (1/2N) sum |D|^2, g = D/N
+      }
+      rx[k] = (R)gx;
+      ry[k] = (R)gy;
+      s3[0] += gx;
+      s3[1] += gy;
+    }
+  }
+  tm.template reduce<3>(s3, sl.a, 0);
+  const R mx = (R)(s3[0] / V), my = (R)(s3[1] / V);
+  const double cost = s3[2];
+  double s2[2] = {0, 0};  // r.z, r.r
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) {
+    const int i = f0 + k * st;
+    if (i < V) {
+      rx[k] -= mx;
+      ry[k] -= my;
+      const R zx = ia[k] * rx[k] + ib[k] * ry[k], zy = ib[k] * rx[k] + ic[k] * ry[k];
+      R2 pz;
+      pz.x = zx;
+      pz.y = zy;
+      pvec[i] = pz;
+      s2[0] += (double)(rx[k] * zx + ry[k] * zy);
+      s2[1] += (double)(rx[k] * rx[k] + ry[k] * ry[k]);
+    }
+  }
+  tm.template reduce<2>(s2, sl.b, 0);
+  double rz = s2[0];
+  const double bnorm = sqrt(s2[1]);
+  double rnorm = bnorm;
+  int status = VX_NOT_CONVERGED, it = 0;
+  if (bnorm == 0.0) status = VX_OK;
+  tm.sync();
+  for (it = 0; status == VX_NOT_CONVERGED && it < ap.max_iter; ++it) {
+    // HVP, cell pass: (2 K_A sA, 2 K_P sP) along p.
+#pragma unroll
+    for (int k = 0; k < MAXC; ++k) {
+      const int c = f0 + k * st;
+      if (c < n) {
+        R sA, sP;
+        cell_dir(vw, c, pvec, sA, sP);
+        R4 q = cell4[c];
+        q.z = k2a[k] * sA;
+        q.w = k2p[k] * sP;
+        cell4[c] = q;
+      }
+    }
+    tm.sync();
+    R hx[MAXV], hy[MAXV], px[MAXV], py[MAXV];
+    double s1[1] = {0};
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      hx[k] = hy[k] = px[k] = py[k] = 0;
+      if (i < V) {
+        vertex_hvp(vw, i, cell4, lam, prm.lam_s, pvec, hx[k], hy[k]);
+        const R2 pp = pvec[i];
+        px[k] = pp.x;
+        py[k] = pp.y;
+        s1[0] += (double)(px[k] * hx[k] + py[k] * hy[k]);
+      }
+    }
+    tm.template reduce<1>(s1, sl.a, 0);
+    if (!(s1[0] > 0)) {
+      status = VX_ERR_INDEFINITE;
+      break;
+    }
+    const R al = (R)(rz / s1[0]);
+    double s2b[2] = {0, 0};
+    R zx[MAXV], zy[MAXV];
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      zx[k] = zy[k] = 0;
+      if (i < V) {
+        lx[k] += al * px[k];
+        ly[k] += al * py[k];
+        rx[k] -= al * hx[k];
+        ry[k] -= al * hy[k];
+        zx[k] = ia[k] * rx[k] + ib[k] * ry[k];
+        zy[k] = ib[k] * rx[k] + ic[k] * ry[k];
+        s2b[0] += (double)(rx[k] * zx[k] + ry[k] * zy[k]);
+        s2b[1] += (double)(rx[k] * rx[k] + ry[k] * ry[k]);
+      }
+    }
+    tm.template reduce<2>(s2b, sl.b, 0);
+    rnorm = sqrt(s2b[1]);
+    if (!(rnorm == rnorm)) {
+      status = VX_ERR_NONFINITE;
+      break;
+    }
+    if (rnorm <= ap.rtol * bnorm) status = VX_OK;
+    const R be = (R)(s2b[0] / rz);
+    rz = s2b[0];
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
+      if (i < V && status == VX_NOT_CONVERGED) {
+        R2 pp;
+        pp.x = zx[k] + be * px[k];
+        pp.y = zy[k] + be * py[k];
+        pvec[i] = pp;
+      }
+    }
+    tm.sync();
+  }
+  tm.sync();
+  // lambda into pvec, then g = -(d^2E/dX dtheta)^T lambda.
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) {
+    const int i = f0 + k * st;
+    if (i < V) {
+      R2 l;
+      l.x = lx[k];
+      l.y = ly[k];
+      pvec[i] = l;
+    }
+  }
+  tm.sync();
+  if (ap.g_lam)
+    for (int e = f0; e < E; e += st) {
+      const int h = 2 * e;
+      const uint32_t tg = vw.tgt[h];
+      const int s = src_of(vw, h), t = tgt_v(tg);
+      R dx, dy;
+      P::diff(vw.X[t], vw.X[s], tgt_ox(tg), tgt_oy(tg), vw.box, dx, dy);
+      const R il = P::rsqrt(dx * dx + dy * dy);
+      const R2 lt = pvec[t], ls = pvec[s];
+      ap.g_lam[e] = -(double)((dx * (lt.x - ls.x) + dy * (lt.y - ls.y)) * il);
+    }
+  if (ap.g_A0 || ap.g_P0)
+    for (int c = f0; c < n; c += st) {
+      R sA, sP;
+      cell_dir(vw, c, pvec, sA, sP);
+      if (ap.g_A0) ap.g_A0[c] = 2.0 * prm.ka(c) * (double)sA;
+      if (ap.g_P0) ap.g_P0[c] = 2.0 * prm.kp(c) * (double)sP;
+    }
+  if (tm.leader() && out) {
+    AdjOut o;
+    o.status = status;
+    o.iters = it;
+    o.rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+    o.cost = cost;
+    *out = o;
+  }
+}
+
+}  // namespace vx

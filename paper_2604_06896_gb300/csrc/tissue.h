@@ -30,6 +30,9 @@ struct vx_tissue_s {
   double* partF;  // per-block FIRE partials
   vx::FireCtrl* ctrl;
   vx::MinOut* dout;
+  // topology at creation (for vx_tissue_restore)
+  uint32_t* tgt0;
+  int32_t *nxt0, *face0, *vout0, *ffirst0;
   // adjoint workspace (float64 vectors [V][2] and per-cell sums)
   double* work;
   size_t work_doubles;
@@ -41,6 +44,8 @@ vx_status energy_forces(vx_tissue_s* t, const double* X, const ParamsD& prm, dou
 vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
                    int check_every, MinOut* out, int* path_used, cudaStream_t s);
 size_t resident_smem_bytes(vx_tissue_s* t);
+vx_status hessian_vector(vx_tissue_s* t, const double* X, const ParamsD& prm, const double* vec,
+                         double* Hv, cudaStream_t s);
 vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
                            const double* dCdX, const vx_grad_opts* o, double* g_lambda, double* g_A0,
                            double* g_P0, vx_grad_result* r, cudaStream_t s);
