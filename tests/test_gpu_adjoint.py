@@ -1,0 +1,133 @@
+"""Equilibrium gradients on the GPU against the FP64 oracle.
+
+The oracle's adjoint (dense factorisation) is pinned against central finite
+differences of the outer cost (tests/test_oracle_solvers.py); here the CUDA
+adjoint (CG on the HVP kernel) and equilibrium propagation are compared with
+it.  Tolerances: FP64 1e-8 relative (CG to rtol 1e-12); FP32 1e-4 relative,
+the bound the workload states for outer gradients.
+"""
+import numpy as np
+import pytest
+
+import vx_inputs as vi
+from oracle import mesh as omesh
+from oracle import model as omodel
+from oracle import solvers as osolv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import paper_2604_06896_gb300 as vx
+    return vx
+
+
+@pytest.fixture(scope="module")
+def equilibrium():
+    """A relaxed 150-cell tissue (oracle, FP64, T1 on) and a v2v target."""
+    c = vi.small_tissue(150, 91, p0=3.7, lam_range=(0.02, 0.1))
+    ref = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    r = osolv.relax(ref["vert"], ref, p, osolv.MinOpts(tol=1e-12, max_iter=100000, dt0=0.01,
+                                                       dt_max=0.5), l_min=5e-3)
+    assert r.converged
+    t = r.tissue
+    t["vert"] = r.X
+    Xt = r.X + 0.05 * np.random.default_rng(92).standard_normal(r.X.shape)
+    return c, t, p, r.X, Xt
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_hvp_parity(vx, equilibrium):
+    import torch
+    c, t, p, X, Xt = equilibrium
+    v = np.random.default_rng(93).standard_normal(X.shape)
+    ref = omodel.hvp(X, t, p, v)
+    for dtype, tol in (("f64", 1e-12), ("f32", 2e-5)):
+        tis = vx.Tissue(t, dtype)
+        Hv = vx.vx_hessian_vector(tis, X, p, v).cpu().numpy()
+        print(f"hvp {dtype}: rel err {rel(Hv, ref):.2e}")
+        assert rel(Hv, ref) < tol
+        tis.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-8), ("f32", 1e-4)])
+@pytest.mark.parametrize("path", ["resident", "cluster"])
+def test_adjoint_parity(vx, equilibrium, dtype, tol, path):
+    c, t, p, X, Xt = equilibrium
+    C, G = omodel.cost_v2v(X, Xt, t)
+    g_ref, _, info = osolv.adjoint_grad(X, t, p, G)
+    assert info["pd"]
+    tis = vx.Tissue(t, dtype)
+    rtol = 1e-12 if dtype == "f64" else 1e-6
+    g, r = vx.vx_equilibrium_grad(tis, X, p, dCdX=G, cg_rtol=rtol, inner=dict(path=path))
+    print(f"adjoint {dtype} {path}: cg {r.cg_iters} it, rel res {r.cg_rel_residual:.1e}; "
+          + ", ".join(f"{k} {rel(g[k].cpu().numpy(), g_ref[k]):.2e}" for k in g_ref))
+    assert r.status == 0
+    for k in ("lam", "A0", "P0"):
+        assert rel(g[k].cpu().numpy(), g_ref[k]) < tol, k
+    # the built-in v2v cost gives the same gradient and reports C
+    g2, r2 = vx.vx_equilibrium_grad(tis, X, p, cost=vx.VX_COST_V2V, cost_data=Xt, cg_rtol=rtol,
+                                    inner=dict(path=path))
+    assert rel(g2["lam"].cpu().numpy(), g_ref["lam"]) < tol
+    assert abs(r2.cost - C) < 1e-10 * C
+    tis.close()
+
+
+def test_adjoint_zero_at_target(vx, equilibrium):
+    c, t, p, X, Xt = equilibrium
+    tis = vx.Tissue(t, "f64")
+    g, r = vx.vx_equilibrium_grad(tis, X, p, cost=vx.VX_COST_V2V, cost_data=X)
+    assert r.status == 0 and r.cg_iters == 0
+    assert max(float(v.abs().max()) for v in g.values()) == 0.0
+    tis.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ep_vs_oracle_and_adjoint(vx, equilibrium, dtype):
+    """Centred EP with the oracle's beta matches the oracle's EP, and both
+    approach the adjoint as O(beta^2)."""
+    c, t, p, X, Xt = equilibrium
+    gradC = lambda Y: omodel.cost_v2v(Y, Xt, t)[1]
+    g_adj, _, _ = osolv.adjoint_grad(X, t, p, gradC(X))
+    beta = 0.2
+    o = osolv.MinOpts(tol=1e-13, max_iter=100000, dt0=0.01, dt_max=0.5)
+    g_ep_ref, _ = osolv.ep_grad(X, t, p, gradC, beta, o, centered=True)
+    tis = vx.Tissue(t, dtype)
+    inner = dict(tol=1e-13 if dtype == "f64" else 1e-7, max_iter=100000, dt0=0.01, dt_max=0.5)
+    g, r = vx.vx_equilibrium_grad(tis, X, p, mode=vx.VX_EP_CENTERED, beta=beta,
+                                  cost=vx.VX_COST_V2V, cost_data=Xt, inner=inner)
+    e_ref = rel(g["lam"].cpu().numpy(), g_ep_ref["lam"])
+    e_adj = rel(g["lam"].cpu().numpy(), g_adj["lam"])
+    print(f"EP {dtype}: nudged iters {r.nudged_iters}; vs oracle EP {e_ref:.2e}; vs adjoint {e_adj:.2e}; "
+          f"oracle EP vs adjoint {rel(g_ep_ref['lam'], g_adj['lam']):.2e}")
+    assert r.status == 0
+    assert e_ref < (1e-7 if dtype == "f64" else 1e-3)
+    assert e_adj < 1e-2
+    tis.close()
+
+
+def test_equilibrium_fn_autograd(vx, equilibrium):
+    """torch.autograd.Function: backward of sum(w * X*) equals the adjoint
+    gradient with dC/dX = w."""
+    import torch
+    c, t, p, X, Xt = equilibrium
+    tis = vx.Tissue(t, "f64")
+    lam = torch.tensor(p["lam"], dtype=torch.float64, device="cuda", requires_grad=True)
+    n = t["n"]
+    A0 = torch.full((n,), float(p["A0"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    P0 = torch.full((n,), float(p["P0"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    X0 = torch.tensor(X, dtype=torch.float64, device="cuda")
+    Xs = vx.EquilibriumFn.apply(X0, lam, A0, P0, tis, p["KA"], p["KP"], dict(tol=1e-12))
+    w = torch.tensor(np.random.default_rng(94).standard_normal(X.shape), device="cuda")
+    (Xs * w).sum().backward()
+    pd = dict(p, A0=np.full(n, p["A0"]), P0=np.full(n, p["P0"]))
+    g_ref, _, _ = osolv.adjoint_grad(Xs.detach().cpu().numpy(), t, pd, w.cpu().numpy())
+    assert rel(lam.grad.cpu().numpy(), g_ref["lam"]) < 1e-7
+    assert rel(A0.grad.cpu().numpy(), g_ref["A0"]) < 1e-7
+    assert rel(P0.grad.cpu().numpy(), g_ref["P0"]) < 1e-7
+    tis.close()

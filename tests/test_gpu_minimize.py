@@ -52,7 +52,7 @@ def polish(top, p, A0, tol=1e-11):
     return d, np.sqrt((F * F).sum(axis=1)).max(), r
 
 
-@pytest.mark.parametrize("path", ["resident", "plain"])
+@pytest.mark.parametrize("path", ["resident", "plain", "cluster"])
 def test_c1_fp64_same_trajectory(vx, path):
     c = vi.tissue_c1()
     ref, p = setup(c)
@@ -64,7 +64,8 @@ def test_c1_fp64_same_trajectory(vx, path):
     print(f"{path}: gpu iters {r.iters} t1 {r.n_t1} st {r.n_stretch} fmax {r.fmax:.3e}; "
           f"oracle iters {ro.iters} t1 {ro.n_t1} st {ro.n_stretch}")
     assert r.converged and r.fmax < 1e-8
-    assert r.path_used == (vx.VX_PATH_RESIDENT if path == "resident" else vx.VX_PATH_PLAIN)
+    assert r.path_used == {"resident": vx.VX_PATH_RESIDENT, "plain": vx.VX_PATH_PLAIN,
+                           "cluster": vx.VX_PATH_CLUSTER}[path]
     check_half_edge_invariants(top)
     assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
     assert np.array_equal(top["he"], ro.tissue["he"])
@@ -75,7 +76,7 @@ def test_c1_fp64_same_trajectory(vx, path):
     assert np.sqrt((Fo * Fo).sum(axis=1)).max() < 1e-8
 
 
-@pytest.mark.parametrize("path", ["resident", "plain"])
+@pytest.mark.parametrize("path", ["resident", "plain", "cluster"])
 def test_fp32_equilibrium_polish(vx, path):
     c = vi.small_tissue(300, 81, p0=3.7, lam_range=(0.02, 0.1))
     ref, p = setup(c)
@@ -126,3 +127,24 @@ def test_not_converged_status(vx):
     ref, p = setup(c)
     r, top = gpu_relax(vx, ref, p, "f32", tol=1e-12, max_iter=10, l_min=5e-3)
     assert r.status == 1 and r.iters == 10
+
+
+def test_c2_full_size_cluster(vx):
+    """The 10,000-cell tissue in the launch configuration the benchmark
+    times (FP32, cluster path, T1 on), checked by the oracle polish."""
+    c = vi.tissue_c2(3.7)
+    ref, p = setup(c)
+    sA = np.sqrt(c["A0"])
+    r, top = gpu_relax(vx, ref, p, "f32", tol=1e-6 * sA, max_iter=200000, dt0=0.01,
+                       dt_max=0.5, l_min=5e-3 * sA)
+    print(f"c2: status {r.status} iters {r.iters} t1 {r.n_t1} st {r.n_stretch} fmax {r.fmax:.2e} "
+          f"path {r.path_used}")
+    assert r.path_used == vx.VX_PATH_CLUSTER
+    check_half_edge_invariants(top)
+    g = omodel.geometry(top["vert"], top)
+    assert abs(g["A"].sum() - 1.0) < 1e-9
+    assert r.converged
+    Fo = omodel.forces(top["vert"], top, p)
+    fo = np.sqrt((Fo * Fo).sum(axis=1)).max()
+    print(f"c2: oracle fmax at X_gpu {fo:.2e}")
+    assert fo < 1e-5 * sA
