@@ -305,6 +305,40 @@ def run_gpu(args):
     print(json.dumps(line))
 
 
+def run_profile(args):
+    """Small fixed-size runs for ncu: the 10,000-cell tissue on the cluster
+    path (capped iterations) and the plain path (capped), and the 100-cell
+    FP64 tissue on the resident path (to convergence)."""
+    import torch
+
+    import paper_2604_06896_gb300 as vx
+    c = vi.tissue_c2(3.7)
+    mesh = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
+    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    t = vx.Tissue(mesh, "f32")
+    for path, iters in (("cluster", args.profile_iters), ("plain", args.profile_iters // 10)):
+        vx.vx_tissue_restore(t)
+        X = torch.tensor(mesh["vert"], dtype=torch.float64, device="cuda")
+        o = opts_for(c["A0"], path)
+        o["max_iter"] = iters
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = vx.vx_minimize(t, X, p, **o)
+        dt = time.perf_counter() - t0
+        print(f"{path}: {r.iters} iterations in {dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
+    F, E = vx.vx_energy_forces(t, X, p)
+    c1 = vi.tissue_c1()
+    m1 = vx.vx_build_mesh(c1["seeds"], c1["Lx"], c1["Ly"])
+    p1 = {k: c1[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    t1 = vx.Tissue(m1, "f64")
+    X1 = torch.tensor(m1["vert"], dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    r = vx.vx_minimize(t1, X1, p1, **opts_for(c1["A0"], "resident") | {"tol": 1e-8})
+    dt = time.perf_counter() - t0
+    print(f"resident c1: {r.iters} iterations in {dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,8 +346,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vx", choices=["vx", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
+    ap.add_argument("--profile-iters", type=int, default=2000)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

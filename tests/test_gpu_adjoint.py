@@ -90,15 +90,17 @@ def test_adjoint_zero_at_target(vx, equilibrium):
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_ep_vs_oracle_and_adjoint(vx, equilibrium, dtype):
     """Centred EP with the oracle's beta matches the oracle's EP, and both
-    approach the adjoint as O(beta^2)."""
+    approach the adjoint as O(beta^2).  FP32 forces carry ~3e-7 relative
+    noise, so the FP32 nudged phases stop at 2e-6 and use a larger beta (the
+    estimate's error is ~ position error / beta)."""
     c, t, p, X, Xt = equilibrium
     gradC = lambda Y: omodel.cost_v2v(Y, Xt, t)[1]
     g_adj, _, _ = osolv.adjoint_grad(X, t, p, gradC(X))
-    beta = 0.2
+    beta = 0.2 if dtype == "f64" else 1.0
     o = osolv.MinOpts(tol=1e-13, max_iter=100000, dt0=0.01, dt_max=0.5)
     g_ep_ref, _ = osolv.ep_grad(X, t, p, gradC, beta, o, centered=True)
     tis = vx.Tissue(t, dtype)
-    inner = dict(tol=1e-13 if dtype == "f64" else 1e-7, max_iter=100000, dt0=0.01, dt_max=0.5)
+    inner = dict(tol=1e-13 if dtype == "f64" else 2e-6, max_iter=100000, dt0=0.01, dt_max=0.5)
     g, r = vx.vx_equilibrium_grad(tis, X, p, mode=vx.VX_EP_CENTERED, beta=beta,
                                   cost=vx.VX_COST_V2V, cost_data=Xt, inner=inner)
     e_ref = rel(g["lam"].cpu().numpy(), g_ep_ref["lam"])
@@ -106,8 +108,8 @@ def test_ep_vs_oracle_and_adjoint(vx, equilibrium, dtype):
     print(f"EP {dtype}: nudged iters {r.nudged_iters}; vs oracle EP {e_ref:.2e}; vs adjoint {e_adj:.2e}; "
           f"oracle EP vs adjoint {rel(g_ep_ref['lam'], g_adj['lam']):.2e}")
     assert r.status == 0
-    assert e_ref < (1e-7 if dtype == "f64" else 1e-3)
-    assert e_adj < 1e-2
+    assert e_ref < (1e-7 if dtype == "f64" else 1e-2)
+    assert e_adj < (1e-4 if dtype == "f64" else 2e-2)
     tis.close()
 
 
