@@ -256,6 +256,59 @@ vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params*
                               double* g_lambda, double* g_A0, double* g_P0,
                               vx_grad_result* r, void* stream);
 
+/* ------------------------------------------------------------ batches */
+
+/*
+ * A batch: many independent tissues of uneven size solved in one persistent
+ * launch (the workload's batched forward path; the paper runs tissues one at
+ * a time).  Tissue k's tables use indices local to the tissue; they are
+ * concatenated in order: he [sum 6 n_k][8], face_he [sum n_k],
+ * edge_id [sum 6 n_k]; box [count][2] = (Lx, Ly).  Positions are the
+ * concatenation of the tissues' [2 n_k][2] arrays.
+ */
+typedef struct vx_batch_s* vx_batch;
+
+typedef struct {
+  const double *KA, *KP, *A0, *P0;  /* dev, per cell [sum n_k] or NULL       */
+  const double* lambda;             /* dev, per edge [sum 3 n_k] or NULL     */
+  const double *KA_t, *KP_t, *A0_t, *P0_t, *lambda_t; /* host, per tissue or NULL */
+  double KA_s, KP_s, A0_s, P0_s, lambda_s;             /* used when both NULL */
+} vx_batch_params;
+
+vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* box,
+                          const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                          int32_t dtype, void* stream, vx_batch* out);
+vx_status vx_batch_destroy(vx_batch b);
+/* Put back every tissue's topology at creation (asynchronous). */
+vx_status vx_batch_restore(vx_batch b, void* stream);
+vx_status vx_batch_sizes(vx_batch b, int32_t* count, int32_t* n_total, int32_t* v_total,
+                         int32_t* e_total);
+/* The batch's current topologies, concatenated in the input format. */
+vx_status vx_batch_topology(vx_batch b, int32_t* he, int32_t* face_he, int32_t* edge_id);
+
+/*
+ * vx_minimize_batched — vx_minimize for every tissue of the batch in one
+ * persistent launch (replayed from a CUDA graph captured at the first call
+ * with these arguments).  CTAs take tissues largest first; a tissue whose
+ * working set fits the CTA's shared-memory allocation is solved there, a
+ * larger one from L2-resident global memory.  X dev float64 [sum V][2]
+ * in/out; r host [count] (out).  opts->path and check_every are ignored.
+ * Synchronises `stream`.
+ */
+vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p,
+                              const vx_min_opts* o, vx_min_result* r, void* stream);
+
+/*
+ * vx_batch_autotune — time `probe_iters`-iteration runs of the batch for
+ * every (threads per CTA, shared memory per CTA) pair in {256, 512, 1024} x
+ * {220, 108, 70} KiB and keep the fastest for later calls (the shared-memory
+ * size is the residency cutoff and sets how many CTAs share an SM).  X is
+ * not modified.  Outputs may be NULL.
+ */
+vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p,
+                            const vx_min_opts* o, int32_t probe_iters, int32_t* threads_out,
+                            int32_t* smem_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # 
 
 __all__ = ["vx_build_mesh", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
            "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "Tissue",
-           "EquilibriumFn", "VxError"]
+           "Batch", "vx_batch_create", "vx_minimize_batched", "vx_batch_autotune",
+           "vx_batch_restore", "EquilibriumFn", "VxError"]
 
 
 def _torch():
@@ -293,3 +294,127 @@ class _Lazy:
 
 
 EquilibriumFn = _Lazy()
+
+
+# ----------------------------------------------------------------- batches
+
+class Batch:
+    """Many tissues solved in one persistent launch (vx_batch)."""
+
+    def __init__(self, meshes, dtype="f32"):
+        self.count = len(meshes)
+        self.n = np.array([int(m["face_he"].shape[0]) for m in meshes], dtype=np.int32)
+        self.V = 2 * self.n
+        self.E = 3 * self.n
+        self.vbase = np.concatenate([[0], np.cumsum(self.V)[:-1]]).astype(np.int64)
+        self.cbase = np.concatenate([[0], np.cumsum(self.n)[:-1]]).astype(np.int64)
+        self.ebase = np.concatenate([[0], np.cumsum(self.E)[:-1]]).astype(np.int64)
+        box = np.ascontiguousarray([[m["Lx"], m["Ly"]] for m in meshes], dtype=np.float64)
+        self.box = box
+        he = np.ascontiguousarray(np.concatenate([m["he"] for m in meshes]), dtype=np.int32)
+        face_he = np.ascontiguousarray(np.concatenate([m["face_he"] for m in meshes]), dtype=np.int32)
+        edge_id = np.ascontiguousarray(np.concatenate([m["edge_id"] for m in meshes]), dtype=np.int32)
+        self.dtype = {"f64": VX_F64, "f32": VX_F32}[dtype] if isinstance(dtype, str) else dtype
+        _torch().cuda.init()
+        h = C.c_void_p()
+        st = capi.vx_batch_create(self.count, self.n.ctypes.data, box.ctypes.data, he.ctypes.data,
+                                  face_he.ctypes.data, edge_id.ctypes.data, self.dtype, _stream(),
+                                  C.byref(h))
+        capi.check(st, "vx_batch_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            capi.vx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, X):
+        return [X[b:b + v] for b, v in zip(self.vbase, self.V)]
+
+    def topologies(self):
+        """Current per-tissue topologies (list of dicts, input format)."""
+        HE = int(6 * self.n.sum())
+        he = np.zeros((HE, 8), dtype=np.int32)
+        face_he = np.zeros(int(self.n.sum()), dtype=np.int32)
+        edge_id = np.zeros(HE, dtype=np.int32)
+        capi.check(capi.vx_batch_topology(self.handle, he.ctypes.data, face_he.ctypes.data,
+                                          edge_id.ctypes.data), "vx_batch_topology")
+        out, h0 = [], 0
+        for k in range(self.count):
+            n = int(self.n[k])
+            out.append(dict(he=he[h0:h0 + 6 * n], face_he=face_he[self.cbase[k]:self.cbase[k] + n],
+                            edge_id=edge_id[h0:h0 + 6 * n], n=n, Lx=self.box[k, 0],
+                            Ly=self.box[k, 1]))
+            h0 += 6 * n
+        return out
+
+
+def make_batch_params(p, b: Batch):
+    """vx_batch_params from a dict: each of KA, KP, A0, P0, lam is a scalar,
+    a per-tissue list/array of length count ('per tissue'), or a device
+    array over all cells / edges of the batch."""
+    keep = []
+    out = capi.vx_batch_params()
+    for key, fp, ft, fs, tot in (("KA", "KA", "KA_t", "KA_s", int(b.n.sum())),
+                                 ("KP", "KP", "KP_t", "KP_s", int(b.n.sum())),
+                                 ("A0", "A0", "A0_t", "A0_s", int(b.n.sum())),
+                                 ("P0", "P0", "P0_t", "P0_s", int(b.n.sum())),
+                                 ("lam", "lambda_", "lambda_t", "lambda_s", int(b.E.sum()))):
+        v = p[key]
+        setattr(out, fp, None)
+        setattr(out, ft, None)
+        setattr(out, fs, 0.0)
+        if np.ndim(v) == 0 and not (hasattr(v, "dim") and v.dim() > 0):
+            setattr(out, fs, float(v))
+        elif (hasattr(v, "numel") and v.numel() == tot) or (not hasattr(v, "numel") and np.size(v) == tot
+                                                          and tot != b.count):
+            t = _dev_f64(v)
+            keep.append(t)
+            setattr(out, fp, t.data_ptr())
+        else:
+            a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+            if a.size != b.count:
+                raise ValueError(f"{key}: expected a scalar, {b.count} per-tissue values or {tot}")
+            keep.append(a)
+            setattr(out, ft, a.ctypes.data)
+    return out, keep
+
+
+def vx_batch_create(meshes, dtype="f32"):
+    return Batch(meshes, dtype)
+
+
+def vx_batch_restore(b: Batch):
+    capi.check(capi.vx_batch_restore(b.handle, _stream()), "vx_batch_restore")
+
+
+def vx_minimize_batched(b: Batch, X, params, **opts):
+    """Relax every tissue of the batch (X: device f64 [sum V, 2], in place).
+    Returns a list of MinResult."""
+    if not (hasattr(X, "is_cuda") and X.is_cuda and X.dtype == _torch().float64
+            and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (updated in place)")
+    prm, keep = make_batch_params(params, b)
+    o = min_opts(**opts)
+    r = (capi.vx_min_result * b.count)()
+    st = capi.vx_minimize_batched(b.handle, _ptr(X), C.byref(prm), C.byref(o), r, _stream())
+    capi.check(st, "vx_minimize_batched")
+    return [MinResult(x.status, x.iters, x.n_t1, x.n_stretch, x.n_short_edges, x.n_inverted,
+                      x.fmax, x.energy, x.path_used, x.force_evals) for x in r]
+
+
+def vx_batch_autotune(b: Batch, X, params, probe_iters=200, **opts):
+    prm, keep = make_batch_params(params, b)
+    o = min_opts(**opts)
+    T = C.c_int32()
+    S = C.c_int32()
+    st = capi.vx_batch_autotune(b.handle, _ptr(X), C.byref(prm), C.byref(o), probe_iters,
+                                C.byref(T), C.byref(S), _stream())
+    capi.check(st, "vx_batch_autotune")
+    return T.value, S.value

@@ -69,6 +69,15 @@ class vx_grad_result(C.Structure):
                 ("cost", C.c_double), ("nudged_iters", C.c_int32 * 2)]
 
 
+class vx_batch_params(C.Structure):
+    _fields_ = [("KA", C.c_void_p), ("KP", C.c_void_p), ("A0", C.c_void_p), ("P0", C.c_void_p),
+                ("lambda_", C.c_void_p),
+                ("KA_t", C.c_void_p), ("KP_t", C.c_void_p), ("A0_t", C.c_void_p),
+                ("P0_t", C.c_void_p), ("lambda_t", C.c_void_p),
+                ("KA_s", C.c_double), ("KP_s", C.c_double), ("A0_s", C.c_double),
+                ("P0_s", C.c_double), ("lambda_s", C.c_double)]
+
+
 def _sig(name, res, *args):
     f = getattr(lib, name)
     f.restype = res
@@ -100,10 +109,27 @@ vx_equilibrium_grad = _sig("vx_equilibrium_grad", C.c_int, C.c_void_p, C.c_void_
                            C.POINTER(vx_params), C.c_void_p, C.POINTER(vx_grad_opts), C.c_void_p,
                            C.c_void_p, C.c_void_p, C.POINTER(vx_grad_result), C.c_void_p)
 
+vx_batch_create = _sig("vx_batch_create", C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                       C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p))
+vx_batch_destroy = _sig("vx_batch_destroy", C.c_int, C.c_void_p)
+vx_batch_restore = _sig("vx_batch_restore", C.c_int, C.c_void_p, C.c_void_p)
+vx_batch_sizes = _sig("vx_batch_sizes", C.c_int, C.c_void_p, P_i32, P_i32, P_i32, P_i32)
+vx_batch_topology = _sig("vx_batch_topology", C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_void_p)
+vx_minimize_batched = _sig("vx_minimize_batched", C.c_int, C.c_void_p, C.c_void_p,
+                           C.POINTER(vx_batch_params), C.POINTER(vx_min_opts),
+                           C.c_void_p, C.c_void_p)
+vx_batch_autotune = _sig("vx_batch_autotune", C.c_int, C.c_void_p, C.c_void_p,
+                         C.POINTER(vx_batch_params), C.POINTER(vx_min_opts), C.c_int32,
+                         P_i32, P_i32, C.c_void_p)
+
 EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_tissue_create",
             "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_tissue_restore",
             "vx_hessian_vector", "vx_energy_forces",
-            "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad"]
+            "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad",
+            "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
+            "vx_batch_topology",
+            "vx_minimize_batched", "vx_batch_autotune"]
 
 
 class VxError(RuntimeError):

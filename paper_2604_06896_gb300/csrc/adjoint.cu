@@ -30,6 +30,11 @@ static View<PolF64> topo_view(vx_tissue_s* t, const double* X) {
   v.box = PolF64::make_box(t->Lx, t->Ly);
   v.Lx = t->Lx;
   v.Ly = t->Ly;
+  v.vnb = t->vnb;
+  v.vfc = t->vfc;
+  v.ccnt = t->ccnt;
+  v.ccor = t->ccor;
+  v.cedge = t->cedge;
   return v;
 }
 
@@ -228,6 +233,11 @@ static vx_status hvp_impl(vx_tissue_s* t, const double* X, const ParamsD& prm, c
   v.box = P::make_box(t->Lx, t->Ly);
   v.Lx = t->Lx;
   v.Ly = t->Ly;
+  v.vnb = t->vnb;
+  v.vfc = t->vfc;
+  v.ccnt = t->ccnt;
+  v.ccor = t->ccor;
+  v.cedge = t->cedge;
   using C4 = typename Vec2Of<typename P::R>::T4;
   C4* cell4 = (C4*)t->work;
   const int th = 256;

@@ -1,0 +1,658 @@
+// Many tissues of uneven size in one persistent launch.
+//
+// Every CTA takes tissues from a queue ordered largest-first (longest
+// processing time first) and relaxes each one to the stop rule.  A tissue
+// whose working set fits the CTA's shared-memory allocation is copied there
+// for the whole solve; a larger one runs from L2-resident global memory.  The
+// CTA size and the shared-memory allocation per CTA (hence the residency
+// cutoff and the number of CTAs per SM) come from an autotuner that times
+// short runs of the batch.  The launch (queue reset, kernel, result copy) is
+// captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "persistent.cuh"
+#include "tissue.h"
+#include "vx_internal.h"
+
+struct BatchDesc {
+  int n, V, E, HE;
+  int vbase, cbase, hbase, ebase, sbase, tbase;
+  double Lx, Ly;
+  double KA, KP, A0, P0, lam;
+};
+
+struct vx_batch_s {
+  int device, count, dtype;
+  int n_tot, V_tot, E_tot, HE_tot, sw_tot, tw_tot;
+  std::vector<BatchDesc> desc;
+  std::vector<int> order;
+  std::vector<std::vector<int32_t>> int2ext;  // per tissue: internal -> caller half-edge
+  // device
+  BatchDesc* d_desc;
+  int* d_order;
+  int* d_counter;
+  uint32_t* tgt;
+  int32_t *nxt, *face, *vout, *ffirst;
+  uint32_t* tgt0;
+  int32_t *nxt0, *face0, *vout0, *ffirst0;
+  void *Xw, *vel, *frc, *cellc;
+  uint32_t *shortbits, *touched;
+  vx::MinOut* d_out;
+  // tuning
+  int threads;
+  int smem_bytes;
+  bool tuned;
+  // graph cache
+  cudaGraphExec_t gexec;
+  std::vector<unsigned char> gkey;
+};
+
+namespace vx {
+
+struct BatchArgs {
+  const BatchDesc* desc;
+  const int* order;
+  int* counter;
+  int count;
+  int smem_bytes;
+  const double* X;  // [V_tot][2] in/out
+  double* Xout;
+  uint32_t* tgt;
+  int32_t *nxt, *face, *vout, *ffirst;
+  void *Xw, *vel, *frc, *cellc;
+  uint32_t *shortbits, *touched;
+  const double *KA, *KP, *A0, *P0, *lam;  // per cell / per edge or null
+  MinParams mp;
+  MinOut* out;
+};
+
+__host__ __device__ inline size_t b16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared memory a resident tissue needs in the batched kernel.
+template <class P>
+__host__ __device__ size_t batch_res_bytes(int n, int V, int E, int HE, int T) {
+  using R = typename P::R;
+  return b16(sizeof(typename P::Pos) * V) + 3 * b16(4 * (size_t)HE) + b16(12 * (size_t)V) +
+         b16(4 * (size_t)n) + b16(2 * sizeof(R) * n) + 2 * b16(2 * sizeof(R) * V) +
+         b16(sizeof(R) * E) + b16(4 * (size_t)((E + 31) / 32)) + b16(4 * (size_t)((V + 31) / 32)) +
+         3 * b16(8 * 4 * (size_t)(T / 32 + 1));
+}
+
+template <class P, int T>
+__global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  using Pos = typename P::Pos;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int item;
+  __shared__ double gslots[3][4 * (T / 32 + 1)];
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) item = atomicAdd(g.counter, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= g.count) break;
+    const BatchDesc d = g.desc[g.order[k]];
+    ParamsD prm;
+    prm.KA = g.KA ? g.KA + d.cbase : nullptr;
+    prm.KP = g.KP ? g.KP + d.cbase : nullptr;
+    prm.A0 = g.A0 ? g.A0 + d.cbase : nullptr;
+    prm.P0 = g.P0 ? g.P0 + d.cbase : nullptr;
+    prm.lam = g.lam ? g.lam + d.ebase : nullptr;
+    prm.KA_s = d.KA;
+    prm.KP_s = d.KP;
+    prm.A0_s = d.A0;
+    prm.P0_s = d.P0;
+    prm.lam_s = d.lam;
+    View<P> v;
+    v.vnb = nullptr;
+    v.vfc = nullptr;
+    v.ccnt = nullptr;
+    v.ccor = nullptr;
+    v.cedge = nullptr;
+    v.n = d.n;
+    v.V = d.V;
+    v.E = d.E;
+    v.box = P::make_box(d.Lx, d.Ly);
+    v.Lx = d.Lx;
+    v.Ly = d.Ly;
+    uint32_t* gt = g.tgt + d.hbase;
+    int32_t* gn = g.nxt + d.hbase;
+    int32_t* gf = g.face + d.hbase;
+    int32_t* gv = g.vout + 3 * d.vbase;
+    int32_t* gff = g.ffirst + d.cbase;
+    const double* Xin = g.X + 2 * (size_t)d.vbase;
+    double* Xo = g.Xout + 2 * (size_t)d.vbase;
+    const bool res = batch_res_bytes<P>(d.n, d.V, d.E, d.HE, T) <= (size_t)g.smem_bytes;
+    if (res) {
+      unsigned char* p = smem;
+      v.X = (Pos*)p;                 p += b16(sizeof(Pos) * d.V);
+      v.tgt = (uint32_t*)p;          p += b16(4 * (size_t)d.HE);
+      v.nxt = (int32_t*)p;           p += b16(4 * (size_t)d.HE);
+      v.face = (int32_t*)p;          p += b16(4 * (size_t)d.HE);
+      v.vout = (int32_t*)p;          p += b16(12 * (size_t)d.V);
+      v.ffirst = (int32_t*)p;        p += b16(4 * (size_t)d.n);
+      R2* cell = (R2*)p;             p += b16(2 * sizeof(R) * d.n);
+      R2* vel = (R2*)p;              p += b16(2 * sizeof(R) * d.V);
+      R2* frc = (R2*)p;              p += b16(2 * sizeof(R) * d.V);
+      R* lam = (R*)p;                p += b16(sizeof(R) * d.E);
+      uint32_t* sb = (uint32_t*)p;   p += b16(4 * (size_t)((d.E + 31) / 32));
+      uint32_t* tb = (uint32_t*)p;   p += b16(4 * (size_t)((d.V + 31) / 32));
+      const size_t ssz = b16(8 * 4 * (size_t)(T / 32 + 1));
+      Slots sl;
+      sl.a = (double*)p;             p += ssz;
+      sl.b = (double*)p;             p += ssz;
+      sl.c = (double*)p;
+      for (int h = tid; h < d.HE; h += T) {
+        v.tgt[h] = gt[h];
+        v.nxt[h] = gn[h];
+        v.face[h] = gf[h];
+      }
+      for (int q = tid; q < 3 * d.V; q += T) v.vout[q] = gv[q];
+      for (int c = tid; c < d.n; c += T) v.ffirst[c] = gff[c];
+      for (int e = tid; e < d.E; e += T) lam[e] = (R)prm.la(e);
+      __syncthreads();
+      min_body_mem<P, T>(v, cell, vel, frc, lam, sb, tb, sl, prm, g.mp, Xin, Xo,
+                         g.out + g.order[k]);
+      __syncthreads();
+      for (int h = tid; h < d.HE; h += T) {
+        gt[h] = v.tgt[h];
+        gn[h] = v.nxt[h];
+        gf[h] = v.face[h];
+      }
+      for (int q = tid; q < 3 * d.V; q += T) gv[q] = v.vout[q];
+      for (int c = tid; c < d.n; c += T) gff[c] = v.ffirst[c];
+    } else {
+      v.X = (Pos*)g.Xw + d.vbase;
+      v.tgt = gt;
+      v.nxt = gn;
+      v.face = gf;
+      v.vout = gv;
+      v.ffirst = gff;
+      Slots sl = {gslots[0], gslots[1], gslots[2]};
+      min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+                         prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xin,
+                         Xo, g.out + g.order[k]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class P, int T>
+static cudaError_t launch_batch_t(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
+  // the shared-memory attribute was set by occupancy() before any capture
+  k_min_batch<P, T><<<grid, T, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P>
+static cudaError_t launch_batch(const BatchArgs& a, int T, int grid, size_t smem, cudaStream_t s) {
+  switch (T) {
+    case 256: return launch_batch_t<P, 256>(a, grid, smem, s);
+    case 512: return launch_batch_t<P, 512>(a, grid, smem, s);
+    default: return launch_batch_t<P, 1024>(a, grid, smem, s);
+  }
+}
+
+template <class P>
+static int occupancy(int T, size_t smem) {
+  int b = 0;
+  cudaError_t e = cudaSuccess;
+  switch (T) {
+    case 256:
+      e = cudaFuncSetAttribute(k_min_batch<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 256>, T, smem);
+      break;
+    case 512:
+      e = cudaFuncSetAttribute(k_min_batch<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 512>, T, smem);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_min_batch<P, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 1024>, T, smem);
+  }
+  return e == cudaSuccess ? b : 0;
+}
+
+}  // namespace vx
+
+using vx::set_error;
+
+namespace {
+
+vx_status fail(vx_status s, const std::string& m) {
+  set_error(m);
+  return s;
+}
+
+bool same_key(const std::vector<unsigned char>& a, const unsigned char* b, size_t n) {
+  return a.size() == n && std::memcmp(a.data(), b, n) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* box,
+                          const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                          int32_t dtype, void* stream, vx_batch* out) {
+  if (count < 1 || !n_cells || !box || !he || !face_he || !edge_id || !out)
+    return fail(VX_ERR_INVALID_ARG, "invalid batch arguments");
+  if (dtype != VX_F64 && dtype != VX_F32) return fail(VX_ERR_INVALID_ARG, "dtype");
+  // Build each tissue through the single-tissue path on the host side, which
+  // validates the tables and produces the internal numbering.
+  vx_batch_s* b = new vx_batch_s();
+  cudaGetDevice(&b->device);
+  b->count = count;
+  b->dtype = dtype;
+  b->desc.resize(count);
+  std::vector<uint32_t> tgt;
+  std::vector<int32_t> nxt, face, vout, ff;
+  int nb = 0, vb = 0, hb = 0, eb = 0, sb = 0, tb = 0;
+  size_t hoff = 0, coff = 0;
+  for (int k = 0; k < count; ++k) {
+    const int n = n_cells[k], HE = 6 * n, V = 2 * n, E = 3 * n;
+    if (n < 1) {
+      delete b;
+      return fail(VX_ERR_INVALID_ARG, "every tissue needs cells");
+    }
+    vx_tissue t = nullptr;
+    // host-only validation and internal tables via vx_tissue_create would
+    // allocate device memory per tissue; instead reuse its table logic:
+    const vx_status st = vx_tissue_create(he + 8 * hoff, face_he + coff, edge_id + hoff, n, HE,
+                                          box[2 * k], box[2 * k + 1], dtype, stream, &t);
+    if (st != VX_OK) {
+      delete b;
+      return st;
+    }
+    std::vector<uint32_t> t_tgt(HE);
+    std::vector<int32_t> t_nxt(HE), t_face(HE), t_vout(3 * V), t_ff(n);
+    cudaMemcpy(t_tgt.data(), t->tgt, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
+    cudaMemcpy(t_nxt.data(), t->nxt, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
+    cudaMemcpy(t_face.data(), t->face, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
+    cudaMemcpy(t_vout.data(), t->vout, 12 * (size_t)V, cudaMemcpyDeviceToHost);
+    cudaMemcpy(t_ff.data(), t->ffirst, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    b->int2ext.push_back(t->int2ext);
+    vx_tissue_destroy(t);
+    tgt.insert(tgt.end(), t_tgt.begin(), t_tgt.end());
+    nxt.insert(nxt.end(), t_nxt.begin(), t_nxt.end());
+    face.insert(face.end(), t_face.begin(), t_face.end());
+    vout.insert(vout.end(), t_vout.begin(), t_vout.end());
+    ff.insert(ff.end(), t_ff.begin(), t_ff.end());
+    BatchDesc& d = b->desc[k];
+    d.n = n;
+    d.V = V;
+    d.E = E;
+    d.HE = HE;
+    d.vbase = vb;
+    d.cbase = nb;
+    d.hbase = hb;
+    d.ebase = eb;
+    d.sbase = sb;
+    d.tbase = tb;
+    d.Lx = box[2 * k];
+    d.Ly = box[2 * k + 1];
+    vb += V;
+    nb += n;
+    hb += HE;
+    eb += E;
+    sb += (E + 31) / 32;
+    tb += (V + 31) / 32;
+    hoff += HE;
+    coff += n;
+  }
+  b->n_tot = nb;
+  b->V_tot = vb;
+  b->E_tot = eb;
+  b->HE_tot = hb;
+  b->sw_tot = sb;
+  b->tw_tot = tb;
+  b->order.resize(count);
+  std::iota(b->order.begin(), b->order.end(), 0);
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return b->desc[x].n > b->desc[y].n; });
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  };
+  A((void**)&b->d_desc, sizeof(BatchDesc) * count);
+  A((void**)&b->d_order, 4 * (size_t)count);
+  A((void**)&b->d_counter, 16);
+  A((void**)&b->tgt, 4 * (size_t)hb);
+  A((void**)&b->nxt, 4 * (size_t)hb);
+  A((void**)&b->face, 4 * (size_t)hb);
+  A((void**)&b->vout, 12 * (size_t)vb);
+  A((void**)&b->ffirst, 4 * (size_t)nb);
+  A((void**)&b->tgt0, 4 * (size_t)hb);
+  A((void**)&b->nxt0, 4 * (size_t)hb);
+  A((void**)&b->face0, 4 * (size_t)hb);
+  A((void**)&b->vout0, 12 * (size_t)vb);
+  A((void**)&b->ffirst0, 4 * (size_t)nb);
+  A(&b->Xw, 16 * (size_t)vb);
+  A(&b->vel, 16 * (size_t)vb);
+  A(&b->frc, 16 * (size_t)vb);
+  A(&b->cellc, 16 * (size_t)nb);
+  A((void**)&b->shortbits, 4 * (size_t)sb);
+  A((void**)&b->touched, 4 * (size_t)tb);
+  A((void**)&b->d_out, sizeof(vx::MinOut) * count);
+  if (e != cudaSuccess) {
+    vx_batch_destroy(b);
+    return fail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA,
+                std::string("vx_batch_create: ") + cudaGetErrorString(e));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->d_order, b->order.data(), 4 * (size_t)count, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->tgt0, tgt.data(), 4 * (size_t)hb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->nxt0, nxt.data(), 4 * (size_t)hb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->face0, face.data(), 4 * (size_t)hb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->vout0, vout.data(), 12 * (size_t)vb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b->ffirst0, ff.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, s);
+  b->threads = 512;
+  b->smem_bytes = 220 * 1024;
+  b->tuned = false;
+  b->gexec = nullptr;
+  *out = b;
+  const vx_status r = vx_batch_restore(b, stream);
+  if (r != VX_OK) return r;
+  if (cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(VX_ERR_CUDA, std::string("vx_batch_create: ") + cudaGetErrorString(cudaGetLastError()));
+  return VX_OK;
+}
+
+vx_status vx_batch_destroy(vx_batch b) {
+  if (!b) return VX_OK;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  void* ptrs[] = {b->d_desc, b->d_order, b->d_counter, b->tgt,  b->nxt,   b->face,  b->vout,
+                  b->ffirst, b->tgt0,    b->nxt0,      b->face0, b->vout0, b->ffirst0, b->Xw,
+                  b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete b;
+  return VX_OK;
+}
+
+vx_status vx_batch_restore(vx_batch b, void* stream) {
+  if (!b) return fail(VX_ERR_INVALID_ARG, "NULL batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t hb = b->HE_tot, vb = b->V_tot, nb = b->n_tot;
+  cudaError_t e = cudaMemcpyAsync(b->tgt, b->tgt0, 4 * hb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->nxt, b->nxt0, 4 * hb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->face, b->face0, 4 * hb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->vout, b->vout0, 12 * vb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ffirst, b->ffirst0, 4 * nb, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? VX_OK : fail(VX_ERR_CUDA, cudaGetErrorString(e));
+}
+
+vx_status vx_batch_topology(vx_batch b, int32_t* he, int32_t* face_he, int32_t* edge_id) {
+  if (!b || !he || !face_he || !edge_id) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  std::vector<uint32_t> tgt(b->HE_tot);
+  std::vector<int32_t> nxt(b->HE_tot), face(b->HE_tot), vout(3 * (size_t)b->V_tot), ff(b->n_tot);
+  if (cudaMemcpy(tgt.data(), b->tgt, 4 * tgt.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(nxt.data(), b->nxt, 4 * nxt.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(face.data(), b->face, 4 * face.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(vout.data(), b->vout, 4 * vout.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ff.data(), b->ffirst, 4 * ff.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(VX_ERR_CUDA, "vx_batch_topology: copy failed");
+  for (int k = 0; k < b->count; ++k) {
+    const BatchDesc& d = b->desc[k];
+    const std::vector<int32_t>& i2e = b->int2ext[k];
+    const uint32_t* tg = tgt.data() + d.hbase;
+    const int32_t* vo = vout.data() + 3 * (size_t)d.vbase;
+    for (int hi = 0; hi < d.HE; ++hi) {
+      const int s = vx::tgt_v(tg[hi ^ 1]);
+      int slot = 0;
+      while (slot < 3 && vo[slot * d.V + s] != hi) ++slot;
+      if (slot == 3) return fail(VX_ERR_TOPOLOGY, "device topology is inconsistent");
+      const int prev = vo[((slot + 1) % 3) * d.V + s] ^ 1;
+      int32_t* r = he + 8 * ((size_t)d.hbase + i2e[hi]);
+      r[0] = i2e[prev];
+      r[1] = i2e[nxt[d.hbase + hi]];
+      r[2] = i2e[hi ^ 1];
+      r[3] = s;
+      r[4] = vx::tgt_v(tg[hi]);
+      r[5] = face[d.hbase + hi];
+      r[6] = vx::tgt_ox(tg[hi]);
+      r[7] = vx::tgt_oy(tg[hi]);
+      edge_id[d.hbase + i2e[hi]] = hi >> 1;
+    }
+    for (int c = 0; c < d.n; ++c) face_he[d.cbase + c] = i2e[ff[d.cbase + c]];
+  }
+  return VX_OK;
+}
+
+vx_status vx_batch_sizes(vx_batch b, int32_t* count, int32_t* n_total, int32_t* v_total,
+                         int32_t* e_total) {
+  if (!b) return fail(VX_ERR_INVALID_ARG, "NULL batch");
+  if (count) *count = b->count;
+  if (n_total) *n_total = b->n_tot;
+  if (v_total) *v_total = b->V_tot;
+  if (e_total) *e_total = b->E_tot;
+  return VX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+vx::BatchArgs make_batch_args(vx_batch b, double* X, const vx_batch_params* p, const vx::MinParams& mp) {
+  vx::BatchArgs a = {};
+  a.desc = b->d_desc;
+  a.order = b->d_order;
+  a.counter = b->d_counter;
+  a.count = b->count;
+  a.smem_bytes = b->smem_bytes;
+  a.X = X;
+  a.Xout = X;
+  a.tgt = b->tgt;
+  a.nxt = b->nxt;
+  a.face = b->face;
+  a.vout = b->vout;
+  a.ffirst = b->ffirst;
+  a.Xw = b->Xw;
+  a.vel = b->vel;
+  a.frc = b->frc;
+  a.cellc = b->cellc;
+  a.shortbits = b->shortbits;
+  a.touched = b->touched;
+  a.KA = p->KA;
+  a.KP = p->KP;
+  a.A0 = p->A0;
+  a.P0 = p->P0;
+  a.lam = p->lambda;
+  a.mp = mp;
+  a.out = b->d_out;
+  return a;
+}
+
+// Per-tissue scalars into the descriptors (per-tissue arrays are host
+// arrays here: they are read once per call).
+void set_tissue_params(vx_batch b, const vx_batch_params* p) {
+  for (int k = 0; k < b->count; ++k) {
+    BatchDesc& d = b->desc[k];
+    d.KA = p->KA_t ? p->KA_t[k] : p->KA_s;
+    d.KP = p->KP_t ? p->KP_t[k] : p->KP_s;
+    d.A0 = p->A0_t ? p->A0_t[k] : p->A0_s;
+    d.P0 = p->P0_t ? p->P0_t[k] : p->P0_s;
+    d.lam = p->lambda_t ? p->lambda_t[k] : p->lambda_s;
+  }
+}
+
+vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::MinParams& mp,
+                    int threads, int smem, cudaStream_t s, bool use_graph) {
+  const bool f64 = b->dtype == VX_F64;
+  const int occ = f64 ? vx::occupancy<vx::PolF64>(threads, smem) : vx::occupancy<vx::PolF32>(threads, smem);
+  if (occ < 1) return fail(VX_ERR_CUDA, "batched kernel cannot be resident with this configuration");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(b->count, occ * sms);
+  b->smem_bytes = smem;
+  vx::BatchArgs a = make_batch_args(b, X, p, mp);
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4, s);
+    if (e != cudaSuccess) return e;
+    return f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
+               : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
+  };
+  cudaError_t e;
+  if (!use_graph) {
+    e = enqueue();
+  } else {
+    // Replay the captured launch when the arguments are unchanged.
+    std::vector<unsigned char> key(sizeof(a) + 2 * sizeof(int));
+    std::memcpy(key.data(), &a, sizeof(a));
+    std::memcpy(key.data() + sizeof(a), &threads, sizeof(int));
+    std::memcpy(key.data() + sizeof(a) + sizeof(int), &grid, sizeof(int));
+    if (!b->gexec || !same_key(b->gkey, key.data(), key.size())) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      cudaStream_t cs;
+      cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      cudaGraph_t g;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaStream_t keep = s;
+        s = cs;
+        const cudaError_t e2 = enqueue();
+        s = keep;
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+        if (e == cudaSuccess) {
+          e = cudaGraphInstantiate(&b->gexec, g, 0);
+          cudaGraphDestroy(g);
+        }
+      }
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      b->gkey = key;
+    }
+    e = cudaGraphLaunch(b->gexec, s);
+  }
+  if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+  return VX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p, const vx_min_opts* o,
+                              vx_min_result* r, void* stream) {
+  if (!b || !X || !p || !o || !r) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  if (o->method != VX_FIRE && o->method != VX_GD) return fail(VX_ERR_INVALID_ARG, "method");
+  if (o->max_iter < 0 || o->patience < 1 || !(o->dt0 > 0) || !(o->dt_max > 0))
+    return fail(VX_ERR_INVALID_ARG, "invalid minimiser options");
+  cudaStream_t s = (cudaStream_t)stream;
+  set_tissue_params(b, p);
+  if (cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(VX_ERR_CUDA, "descriptor upload");
+  vx::MinParams mp = {};
+  mp.method = o->method;
+  mp.tol = o->tol;
+  mp.patience = o->patience;
+  mp.max_iter = o->max_iter;
+  mp.gd_lr = o->gd_lr;
+  mp.dt0 = o->dt0;
+  mp.dt_max = o->dt_max;
+  mp.n_min = o->n_min;
+  mp.f_inc = o->f_inc;
+  mp.f_dec = o->f_dec;
+  mp.alpha0 = o->alpha0;
+  mp.f_alpha = o->f_alpha;
+  mp.l_min = o->l_min;
+  const vx_status st = run_batch(b, X, p, mp, b->threads, b->smem_bytes, s, true);
+  if (st != VX_OK) return st;
+  std::vector<vx::MinOut> out(b->count);
+  if (cudaMemcpyAsync(out.data(), b->d_out, sizeof(vx::MinOut) * b->count, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(VX_ERR_CUDA, std::string("vx_minimize_batched: ") + cudaGetErrorString(cudaGetLastError()));
+  for (int k = 0; k < b->count; ++k) {
+    r[k].status = out[k].status;
+    r[k].iters = out[k].iters;
+    r[k].n_t1 = out[k].n_t1;
+    r[k].n_stretch = out[k].n_stretch;
+    r[k].n_short_edges = out[k].n_short;
+    r[k].n_inverted = out[k].n_inverted;
+    r[k].fmax = out[k].fmax;
+    r[k].energy = out[k].energy;
+    r[k].path_used = VX_PATH_RESIDENT;
+    r[k].force_evals = out[k].force_evals;
+  }
+  return VX_OK;
+}
+
+vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p, const vx_min_opts* o,
+                            int32_t probe_iters, int32_t* threads_out, int32_t* smem_out,
+                            void* stream) {
+  if (!b || !X || !p || !o) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  set_tissue_params(b, p);
+  cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
+                  cudaMemcpyHostToDevice, s);
+  // Scratch copy of X: the probes must not move the caller's positions.
+  double* Xs = nullptr;
+  if (cudaMalloc(&Xs, 16 * (size_t)b->V_tot) != cudaSuccess) return fail(VX_ERR_OOM, "autotune scratch");
+  vx::MinParams mp = {};
+  mp.method = o->method;
+  mp.tol = o->tol;
+  mp.patience = o->patience;
+  mp.max_iter = probe_iters > 0 ? probe_iters : 200;
+  mp.gd_lr = o->gd_lr;
+  mp.dt0 = o->dt0;
+  mp.dt_max = o->dt_max;
+  mp.n_min = o->n_min;
+  mp.f_inc = o->f_inc;
+  mp.f_dec = o->f_dec;
+  mp.alpha0 = o->alpha0;
+  mp.f_alpha = o->f_alpha;
+  mp.l_min = o->l_min;
+  const int Ts[3] = {256, 512, 1024};
+  const int Ss[3] = {220 * 1024, 108 * 1024, 70 * 1024};
+  float best = 1e30f;
+  int bt = b->threads, bs = b->smem_bytes;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int T : Ts)
+    for (int S : Ss) {
+      vx_batch_restore(b, stream);
+      cudaMemcpyAsync(Xs, X, 16 * (size_t)b->V_tot, cudaMemcpyDeviceToDevice, s);
+      cudaEventRecord(e0, s);
+      const vx_status st = run_batch(b, Xs, p, mp, T, S, s, false);
+      cudaEventRecord(e1, s);
+      if (st != VX_OK || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bt = T;
+        bs = S;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Xs);
+  vx_batch_restore(b, stream);
+  b->threads = bt;
+  b->smem_bytes = bs;
+  b->tuned = true;
+  if (threads_out) *threads_out = bt;
+  if (smem_out) *smem_out = bs;
+  return cudaStreamSynchronize(s) == cudaSuccess ? VX_OK : fail(VX_ERR_CUDA, "autotune");
+}
+
+}  // extern "C"

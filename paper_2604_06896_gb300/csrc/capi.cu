@@ -202,6 +202,18 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
     }
   }
   for (int c = 0; c < n; ++c) ff[c] = t->ext2int[face_he[c]];
+  for (int c = 0; c < n; ++c) {
+    int h = ff[c], k = 0;
+    do {
+      ++k;
+      h = nxt[h];
+    } while (h != ff[c] && k <= vx::kMaxCorners);
+    if (k > vx::kMaxCorners - 1) {
+      delete t;
+      return invalid("cell " + std::to_string(c) + " has more than " +
+                     std::to_string(vx::kMaxCorners - 1) + " edges");
+    }
+  }
   auto bytes = [](size_t b) { return b < 16 ? (size_t)16 : b; };
   const int nbc = (n + 255) / 256 + 1, nbv = (V + 255) / 256 + 1;
   cudaError_t e = cudaSuccess;
@@ -218,6 +230,11 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   if (e == cudaSuccess) e = cudaMalloc(&t->touched, bytes(4 * (size_t)(V / 32 + 1)));
   if (e == cudaSuccess) e = cudaMalloc(&t->partE, bytes(3 * 8 * (size_t)nbc));
   if (e == cudaSuccess) e = cudaMalloc(&t->partF, bytes(4 * 8 * (size_t)nbv));
+  if (e == cudaSuccess) e = cudaMalloc(&t->vnb, bytes(12 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->vfc, bytes(12 * (size_t)V));
+  if (e == cudaSuccess) e = cudaMalloc(&t->ccnt, bytes(4 * (size_t)n));
+  if (e == cudaSuccess) e = cudaMalloc(&t->ccor, bytes(4 * (size_t)vx::kMaxCorners * n));
+  if (e == cudaSuccess) e = cudaMalloc(&t->cedge, bytes(4 * (size_t)vx::kMaxCorners * n));
   if (e == cudaSuccess) e = cudaMalloc(&t->tgt0, bytes(4 * (size_t)HE));
   if (e == cudaSuccess) e = cudaMalloc(&t->nxt0, bytes(4 * (size_t)HE));
   if (e == cudaSuccess) e = cudaMalloc(&t->face0, bytes(4 * (size_t)HE));
@@ -245,6 +262,7 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst0, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemsetAsync(t->shortbits, 0, 4 * (size_t)(E / 32 + 1), s));
   VX_CUDA_TRY(cudaMemsetAsync(t->touched, 0, 4 * (size_t)(V / 32 + 1), s));
+  VX_CUDA_TRY(vx::rebuild_flat(t, s));
   VX_CUDA_TRY(cudaStreamSynchronize(s));
   *out = t;
   return VX_OK;
@@ -255,7 +273,8 @@ vx_status vx_tissue_destroy(vx_tissue t) {
   void* ptrs[] = {t->tgt,  t->nxt,   t->face,      t->vout,    t->ffirst, t->Xw,
                   t->vel,  t->F,     t->cellc,     t->shortbits, t->touched, t->partE,
                   t->partF, t->ctrl, t->dout,      t->work,    t->tgt0,   t->nxt0,
-                  t->face0, t->vout0, t->ffirst0};
+                  t->face0, t->vout0, t->ffirst0, t->vnb,   t->vfc,    t->ccnt,
+                  t->ccor,  t->cedge};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -271,6 +290,7 @@ vx_status vx_tissue_restore(vx_tissue t, void* stream) {
   VX_CUDA_TRY(cudaMemcpyAsync(t->face, t->face0, 4 * HE, cudaMemcpyDeviceToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(t->vout, t->vout0, 12 * V, cudaMemcpyDeviceToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst, t->ffirst0, 4 * n, cudaMemcpyDeviceToDevice, s));
+  VX_CUDA_TRY(vx::rebuild_flat(t, s));
   return VX_OK;
 }
 

@@ -128,7 +128,19 @@ struct View {
   int n, V, E;
   typename P::Box box;
   double Lx, Ly;
+  // Optional flat tables (global-memory residencies): per vertex the packed
+  // targets and faces of its three out-half-edges, per cell its corners
+  // (vertex + image relative to corner 0) and half-edges.  They replace the
+  // pointer chase through nxt / vout by one level of independent loads; T1
+  // transitions rebuild the entries they invalidate.
+  uint32_t* vnb;    // [3][V]
+  int32_t* vfc;     // [3][V]
+  int32_t* ccnt;    // [n]
+  uint32_t* ccor;   // [n][kMaxCorners]
+  int32_t* cedge;   // [n][kMaxCorners]
 };
+
+constexpr int kMaxCorners = 16;
 
 // Parameters as the caller gave them (float64, per cell / per edge or
 // uniform).
@@ -156,6 +168,38 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
                                               uint32_t* shortbits, double* eline = nullptr,
                                               const ParamsD* prm = nullptr) {
   using R = typename P::R;
+  if (v.ccor) {
+    const int m = v.ccnt[c];
+    const uint32_t* cor = v.ccor + (size_t)c * kMaxCorners;
+    const int32_t* ced = v.cedge + (size_t)c * kMaxCorners;
+    const typename P::Pos X0 = v.X[tgt_v(cor[0])];
+    R qx = 0, qy = 0, A2 = 0, pp = 0;
+    bool flagged = false;
+    double el = 0.0;
+    for (int k = 1; k <= m; ++k) {
+      R nx = 0, ny = 0;
+      if (k < m) {
+        const uint32_t t = cor[k];
+        P::diff(v.X[tgt_v(t)], X0, tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+      }
+      A2 += qx * ny - nx * qy;
+      const R ex = nx - qx, ey = ny - qy;
+      const R l = sqrt(ex * ex + ey * ey);
+      pp += l;
+      const int h = ced[k - 1];
+      if (l < lmin) {
+        atomicOr(&shortbits[h >> 6], 1u << ((h >> 1) & 31));
+        flagged = true;
+      }
+      if (eline) el += 0.5 * prm->la(h >> 1) * (double)l;
+      qx = nx;
+      qy = ny;
+    }
+    A = (R)0.5 * A2;
+    Per = pp;
+    if (eline) *eline = el;
+    return flagged;
+  }
   const int h0 = v.ffirst[c];
   const int v0 = src_of(v, h0);
   const typename P::Pos X0 = v.X[v0];
@@ -201,12 +245,12 @@ __device__ __forceinline__ void vertex_force(const View<P>& v, int i, const Cell
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int h = v.vout[a * v.V + i];
-    const uint32_t tg = v.tgt[h];
+    const uint32_t tg = v.vnb ? v.vnb[a * v.V + i] : v.tgt[h];
     P::diff(v.X[tgt_v(tg)], Xi, tgt_ox(tg), tgt_oy(tg), v.box, dx[a], dy[a]);
     const R r = P::rsqrt(dx[a] * dx[a] + dy[a] * dy[a]);
     ux[a] = dx[a] * r;
     uy[a] = dy[a] * r;
-    const CellC cc = cellc[v.face[h]];
+    const CellC cc = cellc[v.vfc ? v.vfc[a * v.V + i] : v.face[h]];
     cA[a] = (R)cc.x;
     cP[a] = (R)cc.y;
     la[a] = lam ? (R)lam[h >> 1] : (R)lam_s;
@@ -292,6 +336,35 @@ __device__ double cell_energy_d(const View<P>& v, int c, const ParamsD& prm) {
   return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
 }
 
+// Rebuild the flat-table entries of vertex w and of cell c from the
+// half-edge tables (after a T1 rewired them).
+template <class P>
+__device__ void rebuild_vertex(const View<P>& v, int w) {
+  for (int a = 0; a < 3; ++a) {
+    const int h = v.vout[a * v.V + w];
+    v.vnb[a * v.V + w] = v.tgt[h];
+    v.vfc[a * v.V + w] = v.face[h];
+  }
+}
+template <class P>
+__device__ void rebuild_cell(const View<P>& v, int c) {
+  const int h0 = v.ffirst[c];
+  uint32_t* cor = v.ccor + (size_t)c * kMaxCorners;
+  int32_t* ced = v.cedge + (size_t)c * kMaxCorners;
+  int h = h0, k = 0, cx = 0, cy = 0;
+  cor[0] = pack_tgt(src_of(v, h0), 0, 0);
+  do {
+    const uint32_t tg = v.tgt[h];
+    ced[k] = h;
+    cx += tgt_ox(tg);
+    cy += tgt_oy(tg);
+    ++k;
+    if (k < kMaxCorners) cor[k] = pack_tgt(tgt_v(tg), cx, cy);
+    h = v.nxt[h];
+  } while (h != h0 && k < kMaxCorners);
+  v.ccnt[c] = k;
+}
+
 struct T1Stats {
   int n_t1, n_stretch, err;
 };
@@ -341,7 +414,10 @@ __device__ __noinline__ void t1_pass(View<P> v, const ParamsD& prm, double lmin,
       const int kxx = tgt_ox(v.tgt[hn2]), kxy = tgt_oy(v.tgt[hn2]);
       const int kyx = kbx + tgt_ox(v.tgt[hn1]), kyy = kby + tgt_oy(v.tgt[hn1]);
       const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
-      bool allow = face_size(v, h) > 3 && face_size(v, hq) > 3 && C1 != C2 && C1 != C3 &&
+      bool allow = face_size(v, h) > 3 && face_size(v, hq) > 3 &&
+                   (!v.ccor || (face_size(v, ta_p) < kMaxCorners &&
+                                face_size(v, tb_z) < kMaxCorners)) &&
+                   C1 != C2 && C1 != C3 &&
                    C1 != C4 && C2 != C3 && C2 != C4 && C3 != C4 && kyx >= -1 && kyx <= 1 &&
                    kyy >= -1 && kyy <= 1 && kzx >= -1 && kzx <= 1 && kzy >= -1 && kzy <= 1;
       // Geometry in a's frame.
@@ -428,6 +504,13 @@ __device__ __noinline__ void t1_pass(View<P> v, const ParamsD& prm, double lmin,
       }
       if (take_t1) {
         st->n_t1++;
+        if (v.ccor) {
+          const int p = tgt_v(v.tgt[ta_p]), y = tgt_v(v.tgt[hn1]);
+          const int x = tgt_v(v.tgt[hn2]), z = tgt_v(v.tgt[tb_z]);
+          const int ws[6] = {a, b, p, x, y, z};
+          for (int k = 0; k < 6; ++k) rebuild_vertex(v, ws[k]);
+          for (int k = 0; k < 4; ++k) rebuild_cell(v, cells[k]);
+        }
       } else {
         v.X[a] = Xas;
         v.X[b] = Xbs;

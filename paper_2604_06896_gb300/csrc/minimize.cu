@@ -326,7 +326,26 @@ static View<P> make_view(vx_tissue_s* t) {
   v.box = P::make_box(t->Lx, t->Ly);
   v.Lx = t->Lx;
   v.Ly = t->Ly;
+  v.vnb = t->vnb;
+  v.vfc = t->vfc;
+  v.ccnt = t->ccnt;
+  v.ccor = t->ccor;
+  v.cedge = t->cedge;
   return v;
+}
+
+template <class P>
+__global__ void k_rebuild_flat(View<P> v) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int w = tid; w < v.V; w += st) rebuild_vertex(v, w);
+  for (int c = tid; c < v.n; c += st) rebuild_cell(v, c);
+}
+
+cudaError_t rebuild_flat(vx_tissue_s* t, cudaStream_t s) {
+  View<PolF64> v = make_view<PolF64>(t);
+  const int th = 256, nb = (t->V + th - 1) / th;
+  k_rebuild_flat<PolF64><<<nb, th, 0, s>>>(v);
+  return cudaGetLastError();
 }
 
 template <class P>

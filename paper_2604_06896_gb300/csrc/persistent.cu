@@ -52,6 +52,10 @@ struct PersistArgs {
   void* pvec;
   uint32_t* shortbits;
   uint32_t* touched;
+  uint32_t* vnb;
+  int32_t *vfc, *ccnt;
+  uint32_t* ccor;
+  int32_t* cedge;
 };
 
 template <class P>
@@ -69,6 +73,11 @@ __device__ __forceinline__ View<P> global_view(const PersistArgs& g) {
   v.box = P::make_box(g.Lx, g.Ly);
   v.Lx = g.Lx;
   v.Ly = g.Ly;
+  v.vnb = g.vnb;
+  v.vfc = g.vfc;
+  v.ccnt = g.ccnt;
+  v.ccor = g.ccor;
+  v.cedge = g.cedge;
   return v;
 }
 
@@ -122,6 +131,11 @@ __device__ __forceinline__ View<P> load_resident(const PersistArgs& g, unsigned 
   v.box = P::make_box(g.Lx, g.Ly);
   v.Lx = g.Lx;
   v.Ly = g.Ly;
+  v.vnb = nullptr;
+  v.vfc = nullptr;
+  v.ccnt = nullptr;
+  v.ccor = nullptr;
+  v.cedge = nullptr;
   return v;
 }
 
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(T) k_adj_res(PersistArgs g) {
 template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
-  __shared__ double slots[3][4 * (T / 32 + 1)];
+  __shared__ double slots[3][4 * (T / 32 + 2)];
   ClusterTeam<T, NR> tm;
   for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
   for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
@@ -185,7 +199,7 @@ template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_adj_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
   using R4 = typename Vec2Of<typename P::R>::T4;
-  __shared__ double slots[3][4 * (T / 32 + 1)];
+  __shared__ double slots[3][4 * (T / 32 + 2)];
   ClusterTeam<T, NR> tm;
   Slots sl = {slots[0], slots[1], slots[2]};
   adj_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R4*)g.cell, g.prm.lam,
@@ -218,6 +232,11 @@ static PersistArgs make_args(vx_tissue_s* t, const double* Xin, double* Xout, co
   a.pvec = t->vel;
   a.shortbits = t->shortbits;
   a.touched = t->touched;
+  a.vnb = t->vnb;
+  a.vfc = t->vfc;
+  a.ccnt = t->ccnt;
+  a.ccor = t->ccor;
+  a.cedge = t->cedge;
   return a;
 }
 
@@ -328,10 +347,12 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
   PersistArgs a = make_args(t, X, X, prm);
   a.mp = mp;
   cudaError_t e;
-  if (p == VX_PATH_RESIDENT)
+  if (p == VX_PATH_RESIDENT) {
     e = f64 ? dispatch_res<PolF64, false>(t, a, s) : dispatch_res<PolF32, false>(t, a, s);
-  else
+    if (e == cudaSuccess && mp.l_min > 0) e = rebuild_flat(t, s);
+  } else {
     e = f64 ? dispatch_cluster<PolF64, false>(t, a, s) : dispatch_cluster<PolF32, false>(t, a, s);
+  }
   if (e != cudaSuccess) {
     set_error(std::string("persistent minimiser launch: ") + cudaGetErrorString(e));
     return VX_ERR_CUDA;

@@ -293,6 +293,34 @@ template <class P, class VT>
 __device__ __forceinline__ void cell_dir(const View<P>& v, int c, const VT* vec,
                                          typename P::R& sA, typename P::R& sP) {
   using R = typename P::R;
+  if (v.ccor) {
+    const int m = v.ccnt[c];
+    const uint32_t* cor = v.ccor + (size_t)c * kMaxCorners;
+    const int v0 = tgt_v(cor[0]);
+    const typename P::Pos X0 = v.X[v0];
+    const VT w0 = vec[v0];
+    VT w = w0;
+    R qx = 0, qy = 0, a = 0, pp = 0;
+    for (int k = 1; k <= m; ++k) {
+      R nx = 0, ny = 0;
+      VT wn = w0;
+      if (k < m) {
+        const uint32_t t = cor[k];
+        P::diff(v.X[tgt_v(t)], X0, tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+        wn = vec[tgt_v(t)];
+      }
+      a += qx * (R)wn.y - qy * (R)wn.x + (R)w.x * ny - (R)w.y * nx;
+      const R ex = nx - qx, ey = ny - qy;
+      const R rl = P::rsqrt(ex * ex + ey * ey);
+      pp += (ex * ((R)wn.x - (R)w.x) + ey * ((R)wn.y - (R)w.y)) * rl;
+      qx = nx;
+      qy = ny;
+      w = wn;
+    }
+    sA = (R)0.5 * a;
+    sP = pp;
+    return;
+  }
   const int h0 = v.ffirst[c];
   const int v0 = src_of(v, h0);
   const typename P::Pos X0 = v.X[v0];
@@ -332,13 +360,13 @@ __device__ __forceinline__ void vertex_hvp(const View<P>& v, int i, const C4* ce
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int h = v.vout[a * v.V + i];
-    const uint32_t tg = v.tgt[h];
+    const uint32_t tg = v.vnb ? v.vnb[a * v.V + i] : v.tgt[h];
     const int j = tgt_v(tg);
     P::diff(v.X[j], Xi, tgt_ox(tg), tgt_oy(tg), v.box, dx[a], dy[a]);
     il[a] = P::rsqrt(dx[a] * dx[a] + dy[a] * dy[a]);
     ux[a] = dx[a] * il[a];
     uy[a] = dy[a] * il[a];
-    const C4 cc = cell4[v.face[h]];
+    const C4 cc = cell4[v.vfc ? v.vfc[a * v.V + i] : v.face[h]];
     cA[a] = (R)cc.x;
     cP[a] = (R)cc.y;
     zA[a] = (R)cc.z;
@@ -626,6 +654,188 @@ __device__ void adj_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     o.cost = cost;
     *out = o;
   }
+}
+
+}  // namespace vx
+
+namespace vx {
+
+// ------------------------------------------------- minimiser, memory state
+
+// The same iteration as min_body for one CTA, with the per-vertex state
+// (velocities, forces) in arrays instead of registers and the per-cell
+// parameters read where they are needed, so that one kernel serves tissues
+// of any size (the batched path).  `vel` and `frc` may live in shared or
+// global memory.
+template <class P, int T, class LamT>
+__device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell,
+                             typename Vec2Of<typename P::R>::T* vel,
+                             typename Vec2Of<typename P::R>::T* frc, const LamT* lam,
+                             uint32_t* shortbits, uint32_t* touched, Slots sl,
+                             const ParamsD& prm, const MinParams& mp, const double* Xin,
+                             double* Xout, MinOut* out) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  BlockTeam<T> tm;
+  const int n = vw.n, V = vw.V, E = vw.E, tid = threadIdx.x;
+  for (int i = tid; i < V; i += T) {
+    if (Xin) vw.X[i] = P::from_d(Xin[2 * i], Xin[2 * i + 1]);
+    R2 z;
+    z.x = 0;
+    z.y = 0;
+    vel[i] = z;
+  }
+  for (int w = tid; w < (E + 31) / 32; w += T) shortbits[w] = 0;
+  for (int w = tid; w < (V + 31) / 32; w += T) touched[w] = 0;
+  tm.sync();
+  const R lminR = (R)mp.l_min;
+  double dt = mp.dt0, alpha = mp.alpha0, fmx = 0;
+  int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
+  auto cell_pass = [&](R lm) -> bool {
+    bool fl = false;
+    for (int c = tid; c < n; c += T) {
+      R A, Pp;
+      fl |= cell_geometry(vw, c, A, Pp, lm, shortbits);
+      R2 cc;
+      cc.x = (R)(2.0 * prm.ka(c)) * (A - (R)prm.a0(c));
+      cc.y = (R)(2.0 * prm.kp(c)) * (Pp - (R)prm.p0(c));
+      cell[c] = cc;
+    }
+    return fl;
+  };
+  for (it = 0;; ++it) {
+    const bool fl = cell_pass(lminR);
+    if (mp.l_min > 0) {
+      if (__syncthreads_or(fl)) {
+        if (tid == 0) {
+          T1Stats s1 = {0, 0, 0};
+          int nd = 0;
+          t1_pass(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, &nd);
+          n_t1 += s1.n_t1;
+          n_st += s1.n_stretch;
+        }
+        __syncthreads();
+        for (int w = tid; w < (V + 31) / 32; w += T) {
+          uint32_t b = touched[w];
+          touched[w] = 0;
+          while (b) {
+            const int i = (w << 5) + __ffs(b) - 1;
+            b &= b - 1;
+            R2 z;
+            z.x = 0;
+            z.y = 0;
+            vel[i] = z;
+          }
+        }
+        cell_pass((R)0);
+        __syncthreads();
+      }
+    } else {
+      __syncthreads();
+    }
+    double red[4] = {0, 0, 0, 0};
+    for (int i = tid; i < V; i += T) {
+      R fx, fy;
+      vertex_force(vw, i, cell, lam, prm.lam_s, fx, fy);
+      R2 f;
+      f.x = fx;
+      f.y = fy;
+      frc[i] = f;
+      const R2 u = vel[i];
+      const double f2 = (double)(fx * fx + fy * fy);
+      red[0] += f2;
+      red[1] += (double)(fx * u.x + fy * u.y);
+      red[2] += (double)(u.x * u.x + u.y * u.y);
+      red[3] = fmax(red[3], f2);
+    }
+    tm.template reduce<4>(red, sl.a, 1);
+    fmx = sqrt(red[3]);
+    if (!(fmx == fmx) || isinf(fmx)) {
+      status = VX_ERR_NONFINITE;
+      break;
+    }
+    below = (fmx < mp.tol) ? below + 1 : 0;
+    if (below >= mp.patience) {
+      status = VX_OK;
+      break;
+    }
+    if (it >= mp.max_iter) {
+      status = VX_NOT_CONVERGED;
+      break;
+    }
+    R mA = 0, mB = 0;
+    bool zero = true;
+    R dtR;
+    if (mp.method == 1) {
+      dtR = (R)mp.gd_lr;
+    } else {
+      if (red[1] > 0) {
+        mA = (R)(1.0 - alpha);
+        mB = (R)(alpha * sqrt(red[2]) / sqrt(red[0]));
+        zero = false;
+        if (npos > mp.n_min) {
+          dt = fmin(dt * mp.f_inc, mp.dt_max);
+          alpha *= mp.f_alpha;
+        }
+        ++npos;
+      } else {
+        dt *= mp.f_dec;
+        alpha = mp.alpha0;
+        npos = 0;
+      }
+      dtR = (R)dt;
+    }
+    for (int i = tid; i < V; i += T) {
+      const R2 f = frc[i];
+      if (mp.method == 1) {
+        P::add(vw.X[i], dtR * f.x, dtR * f.y);
+        continue;
+      }
+      R2 u = vel[i];
+      R ux = zero ? (R)0 : mA * u.x + mB * f.x;
+      R uy = zero ? (R)0 : mA * u.y + mB * f.y;
+      ux += dtR * f.x;
+      uy += dtR * f.y;
+      u.x = ux;
+      u.y = uy;
+      vel[i] = u;
+      P::add(vw.X[i], dtR * ux, dtR * uy);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  double fin[3] = {0, 0, 0};
+  for (int c = tid; c < n; c += T) {
+    R A, Pp;
+    double el = 0;
+    cell_geometry(vw, c, A, Pp, (R)0, shortbits, &el, &prm);
+    const double dA = (double)A - prm.a0(c), dP = (double)Pp - prm.p0(c);
+    fin[0] += prm.ka(c) * dA * dA + prm.kp(c) * dP * dP + el;
+    fin[1] += (A <= 0) ? 1.0 : 0.0;
+  }
+  if (mp.l_min > 0)
+    for (int e = tid; e < E; e += T) fin[2] += edge_len_d(vw, 2 * e) < mp.l_min ? 1.0 : 0.0;
+  tm.template reduce<3>(fin, sl.c, 0);
+  if (tid == 0 && out) {
+    MinOut o;
+    o.status = status;
+    o.iters = it;
+    o.n_t1 = n_t1;
+    o.n_stretch = n_st;
+    o.n_short = (int)fin[2];
+    o.n_inverted = (int)fin[1];
+    o.force_evals = it + 1;
+    o.pad = 0;
+    o.fmax = fmx;
+    o.energy = fin[0];
+    *out = o;
+  }
+  if (Xout)
+    for (int i = tid; i < V; i += T) {
+      const double2 d = P::to_d(vw.X[i]);
+      Xout[2 * i] = d.x;
+      Xout[2 * i + 1] = d.y;
+    }
 }
 
 }  // namespace vx

@@ -75,6 +75,7 @@ struct ClusterTeam {
     reduce<1>(v, slots, 1);
     return v[0] > 0.0;
   }
+  // `slots` holds (kWarps + 2) * NV doubles.
   template <int NV>
   __device__ __forceinline__ void reduce(double (&v)[NV], double* slots, int nmax) const {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -89,7 +90,7 @@ struct ClusterTeam {
       if (lane == 0) slots[w * NV + k] = x;
     }
     __syncthreads();
-    // CTA total into slot row kWarps
+    // CTA total into row kWarps.
     if (threadIdx.x < NV) {
       const int k = threadIdx.x;
       double s = 0.0;
@@ -100,15 +101,26 @@ struct ClusterTeam {
       slots[kWarps * NV + k] = s;
     }
     cg::this_cluster().sync();
+    // Warp 0 gathers the NR totals through distributed shared memory (lane q
+    // reads rank q) and reduces them with a fixed shuffle tree into row
+    // kWarps + 1; the other warps read that row after the CTA barrier.
+    if (w == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int q = 0; q < NR; ++q) {
-        const double y = *cg::this_cluster().map_shared_rank(&slots[kWarps * NV + k], q);
-        s = (k >= NV - nmax) ? fmax(s, y) : s + y;
+      for (int k = 0; k < NV; ++k) {
+        const bool mx = k >= NV - nmax;
+        double x = (lane < NR) ? *cg::this_cluster().map_shared_rank(&slots[kWarps * NV + k], lane)
+                               : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = mx ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) slots[(kWarps + 1) * NV + k] = x;
       }
-      v[k] = s;
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = slots[(kWarps + 1) * NV + k];
   }
 };
 

@@ -30,6 +30,11 @@ struct vx_tissue_s {
   double* partF;  // per-block FIRE partials
   vx::FireCtrl* ctrl;
   vx::MinOut* dout;
+  // flat tables (see View): per vertex [3][V], per cell [n][16]
+  uint32_t* vnb;
+  int32_t *vfc, *ccnt;
+  uint32_t* ccor;
+  int32_t* cedge;
   // topology at creation (for vx_tissue_restore)
   uint32_t* tgt0;
   int32_t *nxt0, *face0, *vout0, *ffirst0;
@@ -44,6 +49,9 @@ vx_status energy_forces(vx_tissue_s* t, const double* X, const ParamsD& prm, dou
 vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
                    int check_every, MinOut* out, int* path_used, cudaStream_t s);
 size_t resident_smem_bytes(vx_tissue_s* t);
+// Recompute the flat tables from the half-edge tables (after a resident
+// solve rewrote the latter).
+cudaError_t rebuild_flat(vx_tissue_s* t, cudaStream_t s);
 vx_status hessian_vector(vx_tissue_s* t, const double* X, const ParamsD& prm, const double* vec,
                          double* Hv, cudaStream_t s);
 vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,

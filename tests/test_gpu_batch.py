@@ -1,0 +1,108 @@
+"""Batched minimiser (one persistent launch for many tissues) against the
+FP64 oracle and against itself (graph replay is deterministic)."""
+import numpy as np
+import pytest
+
+import vx_inputs as vi
+from oracle import mesh as omesh
+from oracle import model as omodel
+from oracle import solvers as osolv
+
+from test_oracle_mesh import check_half_edge_invariants
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import paper_2604_06896_gb300 as vx
+    return vx
+
+
+def tissues(sizes, stream0, p0s):
+    out = []
+    for k, (n, p0) in enumerate(zip(sizes, p0s)):
+        c = vi.small_tissue(n, stream0 + k, p0=p0, lam_range=(0.02, 0.1))
+        m = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+        out.append((c, m))
+    return out
+
+
+def test_batch_fp64_matches_oracle(vx):
+    import torch
+    sizes = [30, 120, 45, 80, 200, 60, 150, 35]
+    p0s = [3.6 + 0.03 * k for k in range(len(sizes))]
+    ts = tissues(sizes, 500, p0s)
+    b = vx.Batch([m for _, m in ts], "f64")
+    X = torch.tensor(np.concatenate([m["vert"] for _, m in ts]), dtype=torch.float64, device="cuda")
+    lam = np.concatenate([c["lam"] for c, _ in ts])
+    params = dict(KA=1.0, KP=1.0, A0=1.0, P0=np.array(p0s), lam=torch.tensor(lam, device="cuda"))
+    rs = vx.vx_minimize_batched(b, X, params, tol=1e-9, max_iter=50000, dt0=0.01, dt_max=0.5,
+                                l_min=5e-3)
+    tops = b.topologies()
+    Xs = b.split(X.cpu().numpy())
+    for k, ((c, m), r) in enumerate(zip(ts, rs)):
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=p0s[k], lam=c["lam"])
+        ro = osolv.relax(m["vert"], m, p, osolv.MinOpts(tol=1e-9, max_iter=50000, dt0=0.01,
+                                                        dt_max=0.5), l_min=5e-3)
+        print(f"tissue {k} n={sizes[k]}: gpu {r.iters} it {r.n_t1} T1; oracle {ro.iters} it {ro.n_t1} T1")
+        assert r.converged and ro.converged
+        assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
+        assert abs(r.iters - ro.iters) <= 2
+        assert np.array_equal(tops[k]["he"], ro.tissue["he"])
+        assert np.abs(Xs[k] - ro.X).max() < 1e-6
+    b.close()
+
+
+def test_batch_fp32_mixed_residency_and_replay(vx):
+    """Tissues that fit shared memory and one that does not (global-memory
+    residency) in the same launch; a second call after restoring the
+    topology replays the captured graph and gives identical results."""
+    import torch
+    sizes = [300, 2500, 120, 800, 60, 1500]
+    p0s = [3.7] * len(sizes)
+    ts = tissues(sizes, 600, p0s)
+    b = vx.Batch([m for _, m in ts], "f32")
+    X0 = torch.tensor(np.concatenate([m["vert"] for _, m in ts]), dtype=torch.float64, device="cuda")
+    lam = torch.tensor(np.concatenate([c["lam"] for c, _ in ts]), device="cuda")
+    params = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=lam)
+    kw = dict(tol=1e-6, max_iter=40000, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    X1 = X0.clone()
+    r1 = vx.vx_minimize_batched(b, X1, params, **kw)
+    tops = b.topologies()
+    Xs = b.split(X1.cpu().numpy())
+    for k, ((c, m), r) in enumerate(zip(ts, r1)):
+        top = dict(tops[k])
+        check_half_edge_invariants(dict(top, vert=Xs[k]))
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=c["lam"])
+        F = omodel.forces(Xs[k], top, p)
+        fo = np.sqrt((F * F).sum(axis=1)).max()
+        E = omodel.energy(Xs[k], top, p)
+        print(f"tissue {k} n={sizes[k]}: status {r.status} it {r.iters} T1 {r.n_t1} fmax {r.fmax:.2e} oracle {fo:.2e}")
+        assert r.status in (0, 1)
+        assert abs(r.energy - E) < 1e-5 * abs(E)
+        assert fo < 2e-6 + 2 * r.fmax
+    vx.vx_batch_restore(b)
+    X2 = X0.clone()
+    r2 = vx.vx_minimize_batched(b, X2, params, **kw)
+    assert [r.iters for r in r1] == [r.iters for r in r2]
+    assert torch.equal(X1, X2)
+    b.close()
+
+
+def test_batch_autotune(vx):
+    import torch
+    sizes = [200, 400, 900, 150]
+    ts = tissues(sizes, 700, [3.7] * 4)
+    b = vx.Batch([m for _, m in ts], "f32")
+    X = torch.tensor(np.concatenate([m["vert"] for _, m in ts]), dtype=torch.float64, device="cuda")
+    lam = torch.tensor(np.concatenate([c["lam"] for c, _ in ts]), device="cuda")
+    params = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=lam)
+    kw = dict(tol=1e-6, max_iter=40000, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    X0 = X.clone()
+    T, S = vx.vx_batch_autotune(b, X, params, probe_iters=100, **kw)
+    assert T in (256, 512, 1024) and S > 0
+    assert torch.equal(X, X0)   # probes do not move the caller's positions
+    rs = vx.vx_minimize_batched(b, X, params, **kw)
+    assert all(r.status in (0, 1) for r in rs)
+    b.close()
