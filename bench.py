@@ -328,6 +328,15 @@ def run_profile(args):
             dt = time.perf_counter() - t0
         print(f"{path}: {r.iters} iterations, {r.n_t1} T1, {r.n_stretch} stretches in "
               f"{dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
+        if path == "cluster":
+            # steady state: continue from the relaxed state (few T1 events left)
+            o["max_iter"] = iters
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = vx.vx_minimize(t, X, p, **o)
+            dt = time.perf_counter() - t0
+            print(f"cluster (continued): {r.iters} iterations, {r.n_t1} T1, {r.n_stretch} "
+                  f"stretches in {dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
     F, E = vx.vx_energy_forces(t, X, p)
     c1 = vi.tissue_c1()
     m1 = vx.vx_build_mesh(c1["seeds"], c1["Lx"], c1["Ly"])

@@ -130,10 +130,9 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     const bool fl = cell_pass(lminR);
     if (mp.l_min > 0) {
       if (tm.sync_or(fl, sl.b)) {
-        if (tm.leader()) {
+        if (tm.rank() == 0 && threadIdx.x < 32) {
           T1Stats s1 = {0, 0, 0};
-          int nd = 0;
-          t1_pass(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, &nd);
+          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
         }
@@ -707,10 +706,9 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     const bool fl = cell_pass(lminR);
     if (mp.l_min > 0) {
       if (__syncthreads_or(fl)) {
-        if (tid == 0) {
+        if (tid < 32) {
           T1Stats s1 = {0, 0, 0};
-          int nd = 0;
-          t1_pass(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, &nd);
+          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
         }
