@@ -73,6 +73,102 @@ __global__ void k_v2v_cost(View<PolF64> v, const double* Xt, double* out) {
   }
 }
 
+// ------------------------------------------------ anisotropy outer cost
+
+// Per cell: corner count k, centroid (absolute, unwrapped from corner 0) and
+// the shape tensor S = (1/k) sum (q - c)(q - c)^T; per-block sums of S.
+__global__ void k_aniso_cells(View<PolF64> v, double2* cent, int* kk, double* part) {
+  __shared__ double red[3][32];
+  double s[3] = {0, 0, 0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.n; c += gridDim.x * blockDim.x) {
+    const int h0 = v.ffirst[c];
+    const int v0 = src_of(v, h0);
+    const double2 X0 = v.X[v0];
+    double qx[kMaxCorners * 2], qy[kMaxCorners * 2];
+    qx[0] = 0;
+    qy[0] = 0;
+    int m = 1, cx = 0, cy = 0, h = h0;
+    double mx = 0, my = 0;
+    do {
+      const uint32_t tg = v.tgt[h];
+      cx += tgt_ox(tg);
+      cy += tgt_oy(tg);
+      h = v.nxt[h];
+      if (h != h0) {
+        const double2 Xt = v.X[tgt_v(tg)];
+        qx[m] = (Xt.x + cx * v.Lx) - X0.x;
+        qy[m] = (Xt.y + cy * v.Ly) - X0.y;
+        ++m;
+      }
+    } while (h != h0 && m < 2 * kMaxCorners);
+    for (int k = 0; k < m; ++k) {
+      mx += qx[k];
+      my += qy[k];
+    }
+    mx /= m;
+    my /= m;
+    double sxx = 0, syy = 0, sxy = 0;
+    for (int k = 0; k < m; ++k) {
+      const double wx = qx[k] - mx, wy = qy[k] - my;
+      sxx += wx * wx;
+      syy += wy * wy;
+      sxy += wx * wy;
+    }
+    cent[c] = make_double2(X0.x + mx, X0.y + my);
+    kk[c] = m;
+    s[0] += sxx / m;
+    s[1] += syy / m;
+    s[2] += sxy / m;
+  }
+  for (int q = 0; q < 3; ++q) {
+    double x = warp_sum(s[q]);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
+    part[3 * blockIdx.x + threadIdx.x] = x;
+  }
+}
+
+// Q = mean S, q = ((Qxx - Qyy)/tr Q, 2 Qxy / tr Q), C = |q - q_target|^2 and
+// G = dC/dQ into g[0..3] = (C, Gxx, Gyy, Gxy).
+__global__ void k_aniso_final(const double* part, int nb, int n, const double* qt, double* g) {
+  if (threadIdx.x || blockIdx.x) return;
+  double Q[3] = {0, 0, 0};
+  for (int b = 0; b < nb; ++b)
+    for (int q = 0; q < 3; ++q) Q[q] += part[3 * b + q];
+  const double Qxx = Q[0] / n, Qyy = Q[1] / n, Qxy = Q[2] / n, T = Qxx + Qyy;
+  const double q1 = (Qxx - Qyy) / T, q2 = 2.0 * Qxy / T;
+  const double r1 = 2.0 * (q1 - qt[0]), r2 = 2.0 * (q2 - qt[1]);
+  g[0] = (q1 - qt[0]) * (q1 - qt[0]) + (q2 - qt[1]) * (q2 - qt[1]);
+  g[1] = r1 * 2.0 * Qyy / (T * T) - r2 * 2.0 * Qxy / (T * T);
+  g[2] = -r1 * 2.0 * Qxx / (T * T) - r2 * 2.0 * Qxy / (T * T);
+  g[3] = r2 * 2.0 / T;
+}
+
+// dC/dx_i = sum over the cells of i of (1 / (n k)) (2 Gxx wx + Gxy wy,
+// 2 Gyy wy + Gxy wx), w = x_i - centroid (minimum image).
+__global__ void k_aniso_grad(View<PolF64> v, const double2* cent, const int* kk, const double* g,
+                             double2* out) {
+  const double Gxx = g[1], Gyy = g[2], Gxy = g[3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.V; i += gridDim.x * blockDim.x) {
+    const double2 x = v.X[i];
+    double gx = 0, gy = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int c = v.face[v.vout[a * v.V + i]];
+      double wx = x.x - cent[c].x, wy = x.y - cent[c].y;
+      wx -= v.Lx * rint(wx / v.Lx);
+      wy -= v.Ly * rint(wy / v.Ly);
+      const double s = 1.0 / ((double)v.n * kk[c]);
+      gx += s * (2.0 * Gxx * wx + Gxy * wy);
+      gy += s * (2.0 * Gyy * wy + Gxy * wx);
+    }
+    out[i] = make_double2(gx, gy);
+  }
+}
+
 static bool ensure_work(vx_tissue_s* t, size_t doubles) {
   if (t->work_doubles >= doubles) return true;
   if (t->work) cudaFree(t->work);
@@ -86,13 +182,43 @@ static bool ensure_work(vx_tissue_s* t, size_t doubles) {
 vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
                            const double* dCdX, const vx_grad_opts* o, double* g_lambda, double* g_A0,
                            double* g_P0, vx_grad_result* r, cudaStream_t s) {
-  if (o->cost == VX_COST_ANISO) {
-    set_error("the anisotropy cost is not available in this build");
+  if (o->cost == VX_COST_ANISO && o->mode != VX_ADJOINT_CG) {
+    set_error("equilibrium propagation with the anisotropy cost is not available in this build");
     return VX_ERR_INVALID_ARG;
+  }
+  double* aniso_grad = nullptr;
+  double aniso_cost = 0.0;
+  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_ANISO) {
+    // C and grad_X C of the shape-tensor anisotropy, in FP64, into a buffer
+    // of its own (the adjoint workspace may be reallocated by the solve).
+    const int nb = (t->n + 255) / 256;
+    const size_t need = 2 * (size_t)t->V + 2 * (size_t)t->n + (size_t)t->n + 3 * (size_t)nb + 8;
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, 8 * need) != cudaSuccess) {
+      set_error("out of device memory for the anisotropy cost");
+      return VX_ERR_OOM;
+    }
+    double* gradX = buf;
+    double2* cent = (double2*)(buf + 2 * (size_t)t->V);
+    int* kk = (int*)(buf + 2 * (size_t)t->V + 2 * (size_t)t->n);
+    double* part = buf + 2 * (size_t)t->V + 3 * (size_t)t->n;
+    double* g = part + 3 * (size_t)nb;
+    View<PolF64> vs = topo_view(t, Xstar);
+    vs.ccor = nullptr;
+    k_aniso_cells<<<nb, 256, 0, s>>>(vs, cent, kk, part);
+    k_aniso_final<<<1, 32, 0, s>>>(part, nb, t->n, o->cost_data, g);
+    k_aniso_grad<<<(t->V + 255) / 256, 256, 0, s>>>(vs, cent, kk, g, (double2*)gradX);
+    if (cudaMemcpyAsync(&aniso_cost, g, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaFree(buf);
+      set_error(std::string("anisotropy cost: ") + cudaGetErrorString(cudaGetLastError()));
+      return VX_ERR_CUDA;
+    }
+    aniso_grad = buf;
   }
   if (o->mode == VX_ADJOINT_CG) {
     AdjParams ap = {};
-    ap.dCdX = dCdX;
+    ap.dCdX = aniso_grad ? aniso_grad : dCdX;
     ap.cost = o->cost;
     ap.cost_data = o->cost_data;
     ap.rtol = o->cg_rtol;
@@ -102,11 +228,12 @@ vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& p
     ap.g_P0 = g_P0;
     AdjOut out = {};
     const vx_status st = adjoint_solve(t, Xstar, prm, ap, o->inner.path, &out, s);
+    if (aniso_grad) cudaFree(aniso_grad);
     if (st != VX_OK) return st;
     r->status = out.status;
     r->cg_iters = out.iters;
     r->cg_rel_residual = out.rel_residual;
-    r->cost = dCdX ? 0.0 : out.cost;
+    r->cost = dCdX ? 0.0 : (aniso_grad ? aniso_cost : out.cost);
     r->nudged_iters[0] = r->nudged_iters[1] = 0;
     if (out.status == VX_ERR_INDEFINITE) {
       set_error("CG met a direction of non-positive curvature (the Hessian is not positive definite)");

@@ -136,3 +136,24 @@ def test_equilibrium_fn_autograd(vx, equilibrium):
     assert rel(A0.grad.cpu().numpy(), g_ref["A0"]) < 1e-7
     assert rel(P0.grad.cpu().numpy(), g_ref["P0"]) < 1e-7
     tis.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-8), ("f32", 1e-4)])
+def test_adjoint_anisotropy_cost(vx, equilibrium, dtype, tol):
+    """The shape-tensor anisotropy cost of the inverse-design workload:
+    C and the adjoint gradient against the oracle (whose cost gradient is
+    pinned against finite differences)."""
+    c, t, p, X, Xt = equilibrium
+    qt = (0.1, 0.0)
+    C, G = omodel.shape_tensor_anisotropy(X, t, qt)
+    g_ref, _, _ = osolv.adjoint_grad(X, t, p, G)
+    tis = vx.Tissue(t, dtype)
+    g, r = vx.vx_equilibrium_grad(tis, X, p, cost=vx.VX_COST_ANISO, cost_data=np.array(qt),
+                                  cg_rtol=1e-12 if dtype == "f64" else 1e-6)
+    print(f"aniso {dtype}: C {r.cost:.6e} vs {C:.6e}; cg {r.cg_iters}; "
+          + ", ".join(f"{k} {rel(g[k].cpu().numpy(), g_ref[k]):.2e}" for k in g_ref))
+    assert r.status == 0
+    assert abs(r.cost - C) < 1e-10 * abs(C)
+    for k in ("lam", "A0", "P0"):
+        assert rel(g[k].cpu().numpy(), g_ref[k]) < tol, k
+    tis.close()
