@@ -73,7 +73,7 @@ enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
  *             solve (tissues up to ~1,500 cells in FP32);
  *   CLUSTER:  a 16-CTA thread-block cluster holds it in L2-resident global
  *             memory, synchronised by the hardware cluster barrier (up to
- *             65,536 cells);
+ *             16,384 cells);
  *   PLAIN:    one kernel launch per sub-step, convergence polled by the
  *             host every check_every steps (the reference GPU path).
  *   AUTO picks RESIDENT, then CLUSTER, then PLAIN. */
@@ -300,8 +300,8 @@ vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p,
 
 /*
  * vx_batch_autotune — time `probe_iters`-iteration runs of the batch for
- * every (threads per CTA, shared memory per CTA) pair in {256, 512, 1024} x
- * {220, 108, 70} KiB and keep the fastest for later calls (the shared-memory
+ * every (threads per CTA, shared memory per CTA) pair in {128, 256} x
+ * {220, 108, 70, 52} KiB and keep the fastest for later calls (the shared-memory
  * size is the residency cutoff and sets how many CTAs share an SM).  X is
  * not modified.  Outputs may be NULL.
  */

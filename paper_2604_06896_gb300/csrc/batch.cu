@@ -196,30 +196,24 @@ static cudaError_t launch_batch_t(const BatchArgs& a, int grid, size_t smem, cud
 template <class P>
 static cudaError_t launch_batch(const BatchArgs& a, int T, int grid, size_t smem, cudaStream_t s) {
   switch (T) {
-    case 256: return launch_batch_t<P, 256>(a, grid, smem, s);
-    case 512: return launch_batch_t<P, 512>(a, grid, smem, s);
-    default: return launch_batch_t<P, 1024>(a, grid, smem, s);
+    case 128: return launch_batch_t<P, 128>(a, grid, smem, s);
+    default: return launch_batch_t<P, 256>(a, grid, smem, s);
   }
+}
+
+template <class K>
+static int occ_of(K kernel, int T, size_t smem) {
+  int b = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, T, smem) != cudaSuccess) return 0;
+  return b;
 }
 
 template <class P>
 static int occupancy(int T, size_t smem) {
-  int b = 0;
-  cudaError_t e = cudaSuccess;
-  switch (T) {
-    case 256:
-      e = cudaFuncSetAttribute(k_min_batch<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 256>, T, smem);
-      break;
-    case 512:
-      e = cudaFuncSetAttribute(k_min_batch<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 512>, T, smem);
-      break;
-    default:
-      e = cudaFuncSetAttribute(k_min_batch<P, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_min_batch<P, 1024>, T, smem);
-  }
-  return e == cudaSuccess ? b : 0;
+  return T == 128 ? occ_of(k_min_batch<P, 128>, T, smem) : occ_of(k_min_batch<P, 256>, T, smem);
 }
 
 }  // namespace vx
@@ -356,7 +350,7 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   cudaMemcpyAsync(b->face0, face.data(), 4 * (size_t)hb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b->vout0, vout.data(), 12 * (size_t)vb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b->ffirst0, ff.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, s);
-  b->threads = 512;
+  b->threads = 256;
   b->smem_bytes = 220 * 1024;
   b->tuned = false;
   b->gexec = nullptr;
@@ -617,8 +611,9 @@ vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p, con
   mp.alpha0 = o->alpha0;
   mp.f_alpha = o->f_alpha;
   mp.l_min = o->l_min;
-  const int Ts[3] = {256, 512, 1024};
-  const int Ss[3] = {220 * 1024, 108 * 1024, 70 * 1024};
+  // 128- and 256-thread CTAs hold the loop in registers without spilling
+  const int Ts[2] = {128, 256};
+  const int Ss[4] = {220 * 1024, 108 * 1024, 70 * 1024, 52 * 1024};
   float best = 1e30f;
   int bt = b->threads, bs = b->smem_bytes;
   cudaEvent_t e0, e1;

@@ -15,7 +15,7 @@ vx_status minimize_plain_t(vx_tissue_s* t, double* X, const ParamsD& prm, const 
                            int check_every, MinOut* out_h, cudaStream_t s);
 
 constexpr int kSmemMax = 227 * 1024;
-constexpr int kClusterT = 1024;
+constexpr int kClusterT = 256;  // 255 registers per thread: no spills
 constexpr int kClusterNR = 16;
 
 __host__ __device__ inline size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -248,27 +248,28 @@ static cudaError_t launch_res(K kernel, int T, size_t smem, const PersistArgs& a
   return cudaGetLastError();
 }
 
+// One 256-thread CTA (the largest size whose 255-register budget holds the
+// loop without spilling); each thread owns up to MAXC cells and 2 MAXC
+// vertices.
+constexpr int kResT = 256;
+
 template <class P, bool ADJ>
 static cudaError_t dispatch_res(vx_tissue_s* t, const PersistArgs& a, cudaStream_t s) {
   const int n = t->n;
-  int T;
-  if (n <= 128) T = 128;
-  else if (n <= 256) T = 256;
-  else if (n <= 512) T = 512;
-  else T = 1024;
-  const size_t smem = res_bytes<P>(t->n, t->V, t->E, t->HE, T, ADJ);
+  const size_t smem = res_bytes<P>(t->n, t->V, t->E, t->HE, kResT, ADJ);
+  const int mc = (n + kResT - 1) / kResT;
   if (ADJ) {
-    if (T == 128) return launch_res(k_adj_res<P, 128, 1>, T, smem, a, s);
-    if (T == 256) return launch_res(k_adj_res<P, 256, 1>, T, smem, a, s);
-    if (T == 512) return launch_res(k_adj_res<P, 512, 1>, T, smem, a, s);
-    if (n <= 1024) return launch_res(k_adj_res<P, 1024, 1>, T, smem, a, s);
-    return launch_res(k_adj_res<P, 1024, 2>, T, smem, a, s);
+    if (mc <= 1) return launch_res(k_adj_res<P, kResT, 1>, kResT, smem, a, s);
+    if (mc <= 2) return launch_res(k_adj_res<P, kResT, 2>, kResT, smem, a, s);
+    if (mc <= 3) return launch_res(k_adj_res<P, kResT, 3>, kResT, smem, a, s);
+    if (mc <= 4) return launch_res(k_adj_res<P, kResT, 4>, kResT, smem, a, s);
+    return launch_res(k_adj_res<P, kResT, 6>, kResT, smem, a, s);
   }
-  if (T == 128) return launch_res(k_min_res<P, 128, 1>, T, smem, a, s);
-  if (T == 256) return launch_res(k_min_res<P, 256, 1>, T, smem, a, s);
-  if (T == 512) return launch_res(k_min_res<P, 512, 1>, T, smem, a, s);
-  if (n <= 1024) return launch_res(k_min_res<P, 1024, 1>, T, smem, a, s);
-  return launch_res(k_min_res<P, 1024, 2>, T, smem, a, s);
+  if (mc <= 1) return launch_res(k_min_res<P, kResT, 1>, kResT, smem, a, s);
+  if (mc <= 2) return launch_res(k_min_res<P, kResT, 2>, kResT, smem, a, s);
+  if (mc <= 3) return launch_res(k_min_res<P, kResT, 3>, kResT, smem, a, s);
+  if (mc <= 4) return launch_res(k_min_res<P, kResT, 4>, kResT, smem, a, s);
+  return launch_res(k_min_res<P, kResT, 6>, kResT, smem, a, s);
 }
 
 template <class K>
@@ -297,27 +298,30 @@ static cudaError_t launch_cluster(K kernel, const PersistArgs& a, cudaStream_t s
 template <class P, bool ADJ>
 static cudaError_t dispatch_cluster(vx_tissue_s* t, const PersistArgs& a, cudaStream_t s) {
   const int per = kClusterT * kClusterNR;
+  const int mc = (t->n + per - 1) / per;
   if (ADJ) {
-    if (t->n <= per) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 1>, a, s);
-    if (t->n <= 2 * per) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+    if (mc <= 1) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 1>, a, s);
+    if (mc <= 2) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+    if (mc <= 3) return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 3>, a, s);
     return launch_cluster(k_adj_cluster<P, kClusterT, kClusterNR, 4>, a, s);
   }
-  if (t->n <= per) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 1>, a, s);
-  if (t->n <= 2 * per) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+  if (mc <= 1) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 1>, a, s);
+  if (mc <= 2) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 2>, a, s);
+  if (mc <= 3) return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 3>, a, s);
   return launch_cluster(k_min_cluster<P, kClusterT, kClusterNR, 4>, a, s);
 }
 
 bool resident_fits(vx_tissue_s* t, bool adjoint) {
-  const size_t b = t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, 1024, adjoint)
-                                      : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, 1024, adjoint);
-  return b <= (size_t)kSmemMax && t->n <= 2048;
+  const size_t b = t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, kResT, adjoint)
+                                      : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, kResT, adjoint);
+  return b <= (size_t)kSmemMax && t->n <= 6 * kResT;
 }
 
 bool cluster_fits(vx_tissue_s* t) { return t->n <= 4 * kClusterT * kClusterNR; }
 
 size_t resident_smem_bytes(vx_tissue_s* t) {
-  return t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, 1024, false)
-                            : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, 1024, false);
+  return t->dtype == VX_F64 ? res_bytes<PolF64>(t->n, t->V, t->E, t->HE, kResT, false)
+                            : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, kResT, false);
 }
 
 static int choose_path(vx_tissue_s* t, int path, bool adjoint) {

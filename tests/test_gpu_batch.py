@@ -105,7 +105,7 @@ def test_batch_autotune(vx):
     kw = dict(tol=1e-6, max_iter=40000, dt0=0.01, dt_max=0.5, l_min=5e-3)
     X0 = X.clone()
     T, S = vx.vx_batch_autotune(b, X, params, probe_iters=100, **kw)
-    assert T in (256, 512, 1024) and S > 0
+    assert T in (128, 256) and S > 0
     assert torch.equal(X, X0)   # probes do not move the caller's positions
     rs = vx.vx_minimize_batched(b, X, params, **kw)
     assert all(r.status in (0, 1) for r in rs)
