@@ -256,6 +256,33 @@ vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params*
                               double* g_lambda, double* g_A0, double* g_P0,
                               vx_grad_result* r, void* stream);
 
+/*
+ * vx_energy_forces_noalloc — vx_energy_forces for callers that cannot
+ * allocate device memory (a stream capture whose memory pool is frozen, a
+ * plugin with a fixed memory budget, a real-time loop that must not touch
+ * the allocator).  The paper has no counterpart: this is an interface of the
+ * library, not a step of the method.
+ *
+ * It needs no vx_tissue (creating one allocates).  The caller passes, in its
+ * own device memory, the topology tables in the format of this header
+ * (he int32 [6n][8], face_he int32 [n], edge_id int32 [6n]), X float64
+ * [2n][2], and the outputs F float64 [2n][2] (or NULL) and E float64 [1] (or
+ * NULL), plus status int32 [1], set to 1 when a vertex is not 3-valent.
+ * Arithmetic is FP64.  Nothing is allocated and no allocating library routine
+ * is called: the kernels' scratch lives in one static device array sized for
+ * at most 32,768 cells (about 1.8 MB, held by every GPU that loads the
+ * library until the process exits); larger tissues are rejected with
+ * VX_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (with that device current) and caches it: make that first
+ * call before any stream capture.  All calls share the one array: calls
+ * that overlap on the GPU (on different streams) race and must be ordered
+ * by the caller.  Asynchronous on `stream`.
+ */
+vx_status vx_energy_forces_noalloc(const int32_t* he, const int32_t* face_he,
+                                   const int32_t* edge_id, int32_t n_cells, double Lx, double Ly,
+                                   const double* X, const vx_params* p, double* F, double* E,
+                                   int32_t* status, void* stream);
+
 /* ------------------------------------------------------------ batches */
 
 /*

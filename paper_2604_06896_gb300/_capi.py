@@ -109,6 +109,10 @@ vx_equilibrium_grad = _sig("vx_equilibrium_grad", C.c_int, C.c_void_p, C.c_void_
                            C.POINTER(vx_params), C.c_void_p, C.POINTER(vx_grad_opts), C.c_void_p,
                            C.c_void_p, C.c_void_p, C.POINTER(vx_grad_result), C.c_void_p)
 
+vx_energy_forces_noalloc = _sig("vx_energy_forces_noalloc", C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p,
+                                C.POINTER(vx_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p)
 vx_batch_create = _sig("vx_batch_create", C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                        C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p))
 vx_batch_destroy = _sig("vx_batch_destroy", C.c_int, C.c_void_p)
@@ -128,7 +132,7 @@ EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_tissue_create",
             "vx_hessian_vector", "vx_energy_forces",
             "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad",
             "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
-            "vx_batch_topology",
+            "vx_batch_topology", "vx_energy_forces_noalloc",
             "vx_minimize_batched", "vx_batch_autotune"]
 
 
