@@ -170,7 +170,10 @@ def run_gpu(args):
     cases = []
     for p0 in vi.C2_P0_SWEEP:
         c = vi.tissue_c2(p0)
-        mesh = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
+        # the same seeds, labelled along a Hilbert curve: the same tissue with
+        # spatially ordered cell / vertex / edge numbering (both paths)
+        order = vx.vx_seed_order(c["seeds"], c["Lx"], c["Ly"])
+        mesh = vx.vx_build_mesh(c["seeds"][order], c["Lx"], c["Ly"])
         p = dict(KA=c["KA"], KP=c["KP"], A0=c["A0"], P0=c["P0"], lam=0.05 * math.sqrt(c["A0"]))
         t = vx.Tissue(mesh, "f32")
         X0 = torch.tensor(mesh["vert"], dtype=torch.float64, device=dev)
@@ -282,6 +285,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_t.item() / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_cells": n, "n_vertices": V,
+                   "numbering": "seeds in Hilbert-curve order (vx_seed_order)",
                    "path": {1: "resident", 2: "plain", 3: "cluster"}.get(path_used, path_used),
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -313,7 +317,8 @@ def run_profile(args):
 
     import paper_2604_06896_gb300 as vx
     c = vi.tissue_c2(3.7)
-    mesh = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
+    order = vx.vx_seed_order(c["seeds"], c["Lx"], c["Ly"]) if args.ordered else np.arange(c["n"])
+    mesh = vx.vx_build_mesh(c["seeds"][order], c["Lx"], c["Ly"])
     p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
     t = vx.Tissue(mesh, "f32")
     for path, iters in (("cluster", args.profile_iters), ("plain", args.profile_iters // 10)):
@@ -359,6 +364,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
     ap.add_argument("--profile-iters", type=int, default=2000)
+    ap.add_argument("--ordered", type=int, default=1, help="profile: Hilbert-ordered seeds")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

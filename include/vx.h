@@ -113,6 +113,18 @@ const char* vx_version(void);
 vx_status vx_build_mesh(const double* seeds_xy, int32_t n_cells, double Lx, double Ly,
                         double* vert_xy, int32_t* he, int32_t* face_he, int32_t* edge_id);
 
+/*
+ * vx_seed_order — an ordering of the seeds along a Hilbert curve through the
+ * box (order[k] = index of the k-th seed).  The canonical numbering of
+ * vx_build_mesh follows the seed order, so building from the reordered
+ * seeds gives the same tissue with cells, vertices and edges numbered in
+ * spatial order: neighbouring threads then touch neighbouring memory, which
+ * is what the global-memory kernels need to coalesce their gathers.
+ * seeds_xy host float64 [n][2]; order host int32 [n] (out).
+ */
+vx_status vx_seed_order(const double* seeds_xy, int32_t n_cells, double Lx, double Ly,
+                        int32_t* order);
+
 /* Opaque handle: one tissue (topology on the device + workspace). */
 typedef struct vx_tissue_s* vx_tissue;
 

@@ -18,7 +18,7 @@ from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # 
                     VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
                     VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
 
-__all__ = ["vx_build_mesh", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
+__all__ = ["vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
            "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "Tissue",
            "Batch", "vx_batch_create", "vx_minimize_batched", "vx_batch_autotune",
            "vx_batch_restore", "EquilibriumFn", "VxError"]
@@ -67,6 +67,16 @@ def vx_build_mesh(seeds, Lx, Ly):
     capi.check(st, "vx_build_mesh")
     return dict(vert=vert, he=he, face_he=face_he, edge_id=edge_id, n=n, Lx=float(Lx),
                 Ly=float(Ly))
+
+
+def vx_seed_order(seeds, Lx, Ly):
+    """Hilbert-curve order of the seeds (see vx.h); build from seeds[order]
+    for spatially ordered cell, vertex and edge numbering."""
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64))
+    order = np.zeros(s.shape[0], dtype=np.int32)
+    capi.check(capi.vx_seed_order(s.ctypes.data, s.shape[0], float(Lx), float(Ly),
+                                  order.ctypes.data), "vx_seed_order")
+    return order
 
 
 # ------------------------------------------------------------ parameters

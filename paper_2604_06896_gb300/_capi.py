@@ -89,6 +89,8 @@ vx_last_error = _sig("vx_last_error", C.c_char_p)
 vx_version = _sig("vx_version", C.c_char_p)
 vx_build_mesh = _sig("vx_build_mesh", C.c_int, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+vx_seed_order = _sig("vx_seed_order", C.c_int, C.c_void_p, C.c_int32, C.c_double, C.c_double,
+                     C.c_void_p)
 vx_tissue_create = _sig("vx_tissue_create", C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                         C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_void_p,
                         C.POINTER(C.c_void_p))
@@ -127,7 +129,7 @@ vx_batch_autotune = _sig("vx_batch_autotune", C.c_int, C.c_void_p, C.c_void_p,
                          C.POINTER(vx_batch_params), C.POINTER(vx_min_opts), C.c_int32,
                          P_i32, P_i32, C.c_void_p)
 
-EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_tissue_create",
+EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx_tissue_create",
             "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_tissue_restore",
             "vx_hessian_vector", "vx_energy_forces",
             "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad",

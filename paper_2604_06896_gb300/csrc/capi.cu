@@ -148,6 +148,15 @@ vx_status vx_build_mesh(const double* seeds_xy, int32_t n_cells, double Lx, doub
   return s;
 }
 
+vx_status vx_seed_order(const double* seeds_xy, int32_t n_cells, double Lx, double Ly,
+                        int32_t* order) {
+  if (!seeds_xy || !order) return invalid("NULL pointer");
+  if (n_cells < 1) return invalid("n_cells must be positive");
+  if (!(Lx > 0) || !(Ly > 0)) return invalid("box sides must be positive");
+  vx::seed_order(seeds_xy, n_cells, Lx, Ly, order);
+  return VX_OK;
+}
+
 vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
                            int32_t n_cells, int32_t n_half_edges, double Lx, double Ly,
                            int32_t dtype, void* stream, vx_tissue* out) {

@@ -387,4 +387,39 @@ vx_status build_mesh(const double* seeds, int n, double Lx, double Ly, double* v
   return VX_OK;
 }
 
+// Position of cell (x, y) of a 2^k x 2^k grid along the Hilbert curve:
+// descend the quadrant tree, adding the number of cells in the quadrants the
+// curve visits before this one and turning the frame so that every sub-square
+// is traversed from its entry corner.
+static uint64_t hilbert_index(uint32_t side, uint32_t x, uint32_t y) {
+  uint64_t d = 0;
+  for (uint32_t s = side >> 1; s > 0; s >>= 1) {
+    const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+    d += (uint64_t)s * s * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = side - 1 - x;
+        y = side - 1 - y;
+      }
+      const uint32_t t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
+void seed_order(const double* seeds, int n, double Lx, double Ly, int32_t* order) {
+  const uint32_t side = 1u << 16;
+  std::vector<std::pair<uint64_t, int32_t>> key(n);
+  for (int i = 0; i < n; ++i) {
+    const double fx = seeds[2 * i] / Lx, fy = seeds[2 * i + 1] / Ly;
+    const uint32_t x = (uint32_t)std::min<double>(side - 1, std::max(0.0, fx * side));
+    const uint32_t y = (uint32_t)std::min<double>(side - 1, std::max(0.0, fy * side));
+    key[i] = {hilbert_index(side, x, y), i};
+  }
+  std::sort(key.begin(), key.end());
+  for (int i = 0; i < n; ++i) order[i] = key[i].second;
+}
+
 }  // namespace vx

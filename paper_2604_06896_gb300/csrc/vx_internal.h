@@ -17,4 +17,6 @@ vx_status build_mesh(const double* seeds, int n, double Lx, double Ly, double* v
 
 void set_error(const std::string& msg);
 
+void seed_order(const double* seeds, int n, double Lx, double Ly, int32_t* order);
+
 }  // namespace vx
