@@ -169,31 +169,52 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
                                               const ParamsD* prm = nullptr) {
   using R = typename P::R;
   if (v.ccor) {
+    // Corners in chunks of four: the corner words arrive in one 16-byte load
+    // and the four position loads are issued before any is used, so a cell
+    // costs two load latencies per chunk instead of two per corner.
+    using Pos = typename P::Pos;
     const int m = v.ccnt[c];
     const uint32_t* cor = v.ccor + (size_t)c * kMaxCorners;
     const int32_t* ced = v.cedge + (size_t)c * kMaxCorners;
-    const typename P::Pos X0 = v.X[tgt_v(cor[0])];
     R qx = 0, qy = 0, A2 = 0, pp = 0;
     bool flagged = false;
     double el = 0.0;
-    for (int k = 1; k <= m; ++k) {
-      R nx = 0, ny = 0;
-      if (k < m) {
-        const uint32_t t = cor[k];
-        P::diff(v.X[tgt_v(t)], X0, tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+    Pos X0;
+    for (int base = 0; base < m; base += 4) {
+      const uint4 w0 = reinterpret_cast<const uint4*>(cor + base)[0];
+      const uint32_t cw[4] = {w0.x, w0.y, w0.z, w0.w};
+      Pos Xc[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (base + k < m) Xc[k] = v.X[tgt_v(cw[k])];
+      if (base == 0) X0 = Xc[0];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int kk = base + k;  // edge from corner kk to corner kk + 1
+        if (kk < m) {
+          R nx = 0, ny = 0;
+          if (k < 3) {
+            if (kk + 1 < m)
+              P::diff(Xc[k + 1], X0, tgt_ox(cw[k + 1]), tgt_oy(cw[k + 1]), v.box, nx, ny);
+          } else if (kk + 1 < m) {
+            const uint32_t t = cor[kk + 1];
+            P::diff(v.X[tgt_v(t)], X0, tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+          }
+          // q_kk -> q_{kk+1}; q_0 = 0
+          A2 += qx * ny - nx * qy;
+          const R ex = nx - qx, ey = ny - qy;
+          const R l = sqrt(ex * ex + ey * ey);
+          pp += l;
+          if (l < lmin) {
+            const int h = ced[kk];
+            atomicOr(&shortbits[h >> 6], 1u << ((h >> 1) & 31));
+            flagged = true;
+          }
+          if (eline) el += 0.5 * prm->la(ced[kk] >> 1) * (double)l;
+          qx = nx;
+          qy = ny;
+        }
       }
-      A2 += qx * ny - nx * qy;
-      const R ex = nx - qx, ey = ny - qy;
-      const R l = sqrt(ex * ex + ey * ey);
-      pp += l;
-      const int h = ced[k - 1];
-      if (l < lmin) {
-        atomicOr(&shortbits[h >> 6], 1u << ((h >> 1) & 31));
-        flagged = true;
-      }
-      if (eline) el += 0.5 * prm->la(h >> 1) * (double)l;
-      qx = nx;
-      qy = ny;
     }
     A = (R)0.5 * A2;
     Per = pp;
@@ -234,41 +255,74 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
   return flagged;
 }
 
-// Force on vertex i from the cell coefficients (cA, cP) and edge tensions.
+// Everything the force on one vertex reads, loaded in one go (gather) and
+// used afterwards (compute), so that a thread owning several vertices has
+// all their loads in flight together.
+template <class P>
+struct VGather {
+  typename P::Pos Xi, Xj[3];
+  uint32_t tg[3];
+  typename P::R cA[3], cP[3], la[3];
+};
+
 template <class P, class CellC, class LamT>
-__device__ __forceinline__ void vertex_force(const View<P>& v, int i, const CellC* cellc,
-                                             const LamT* lam, double lam_s, typename P::R& fx,
-                                             typename P::R& fy) {
+__device__ __forceinline__ void vertex_gather(const View<P>& v, int i, const CellC* cellc,
+                                              const LamT* lam, double lam_s, VGather<P>& g) {
   using R = typename P::R;
-  const typename P::Pos Xi = v.X[i];
-  R dx[3], dy[3], ux[3], uy[3], cA[3], cP[3], la[3];
+  int h[3], f[3];
+  g.Xi = v.X[i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int h = v.vout[a * v.V + i];
-    const uint32_t tg = v.vnb ? v.vnb[a * v.V + i] : v.tgt[h];
-    P::diff(v.X[tgt_v(tg)], Xi, tgt_ox(tg), tgt_oy(tg), v.box, dx[a], dy[a]);
+    h[a] = v.vout[a * v.V + i];
+    g.tg[a] = v.vnb ? v.vnb[a * v.V + i] : v.tgt[h[a]];
+    f[a] = v.vfc ? v.vfc[a * v.V + i] : v.face[h[a]];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.Xj[a] = v.X[tgt_v(g.tg[a])];
+    const CellC cc = cellc[f[a]];
+    g.cA[a] = (R)cc.x;
+    g.cP[a] = (R)cc.y;
+    g.la[a] = lam ? (R)lam[h[a] >> 1] : (R)lam_s;
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void vertex_compute(const View<P>& v, const VGather<P>& g,
+                                               typename P::R& fx, typename P::R& fy) {
+  using R = typename P::R;
+  R dx[3], dy[3], ux[3], uy[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P::diff(g.Xj[a], g.Xi, tgt_ox(g.tg[a]), tgt_oy(g.tg[a]), v.box, dx[a], dy[a]);
     const R r = P::rsqrt(dx[a] * dx[a] + dy[a] * dy[a]);
     ux[a] = dx[a] * r;
     uy[a] = dy[a] * r;
-    const CellC cc = cellc[v.vfc ? v.vfc[a * v.V + i] : v.face[h]];
-    cA[a] = (R)cc.x;
-    cP[a] = (R)cc.y;
-    la[a] = lam ? (R)lam[h >> 1] : (R)lam_s;
   }
   R gx = 0, gy = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int am = (a + 2) % 3, ap = (a + 1) % 3;
-    const R T = la[a] + cP[a] + cP[am];
+    const R T = g.la[a] + g.cP[a] + g.cP[am];
     gx += T * ux[a];
     gy += T * uy[a];
     // -1/2 cA rot(d_a - d_{a+1}),  rot(x, y) = (y, -x)
     const R wx = dx[a] - dx[ap], wy = dy[a] - dy[ap];
-    gx -= (R)0.5 * cA[a] * wy;
-    gy += (R)0.5 * cA[a] * wx;
+    gx -= (R)0.5 * g.cA[a] * wy;
+    gy += (R)0.5 * g.cA[a] * wx;
   }
   fx = gx;
   fy = gy;
+}
+
+// Force on vertex i from the cell coefficients (cA, cP) and edge tensions.
+template <class P, class CellC, class LamT>
+__device__ __forceinline__ void vertex_force(const View<P>& v, int i, const CellC* cellc,
+                                             const LamT* lam, double lam_s, typename P::R& fx,
+                                             typename P::R& fy) {
+  VGather<P> g;
+  vertex_gather(v, i, cellc, lam, lam_s, g);
+  vertex_compute(v, g, fx, fy);
 }
 
 // ------------------------------------------------------------ T1 (serial)

@@ -154,8 +154,12 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
 #pragma unroll
     for (int k = 0; k < MAXV; ++k) {
       const int i = f0 + k * st;
+      if (i < V) vertex_force(vw, i, cell, lam, prm.lam_s, fx[k], fy[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int i = f0 + k * st;
       if (i < V) {
-        vertex_force(vw, i, cell, lam, prm.lam_s, fx[k], fy[k]);
         if (nudged) {
           double gx, gy;
           v2v_grad(vw, i, mp.cost_data, gx, gy);
@@ -210,6 +214,12 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
         npos = 0;
       }
       const R dtR = (R)dt;
+      typename P::Pos xs[MAXV];
+#pragma unroll
+      for (int k = 0; k < MAXV; ++k) {
+        const int i = f0 + k * st;
+        if (i < V) xs[k] = vw.X[i];
+      }
 #pragma unroll
       for (int k = 0; k < MAXV; ++k) {
         const int i = f0 + k * st;
@@ -220,7 +230,8 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
           uy += dtR * fy[k];
           vx[k] = ux;
           vy[k] = uy;
-          P::add(vw.X[i], dtR * ux, dtR * uy);
+          P::add(xs[k], dtR * ux, dtR * uy);
+          vw.X[i] = xs[k];
         }
       }
     }
