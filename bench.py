@@ -33,9 +33,12 @@ UNIT = "vertex-force evals/s"
 WORKLOAD = "c2: 10,000-cell periodic Voronoi tissue, FIRE+T1 to max|F|<1e-6*sqrt(A0), p0 in {3.5,3.7,3.9}"
 
 
+MAX_ITER = 20_000   # per relaxation; see the design notes on c2's convergence
+
+
 def opts_for(A0, path):
     sA = math.sqrt(A0)
-    return dict(tol=1e-6 * sA, max_iter=200_000, dt0=0.01, dt_max=0.5, l_min=5e-3 * sA,
+    return dict(tol=1e-6 * sA, max_iter=MAX_ITER, dt0=0.01, dt_max=0.5, l_min=5e-3 * sA,
                 path=path, check_every=100)
 
 
@@ -183,15 +186,18 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(path, stats=None):
-        evals = 0
         for c, mesh, p, t, X0, X in cases:
             vx.vx_tissue_restore(t)
             X.copy_(X0)
-            r = vx.vx_minimize(t, X, p, **opts_for(c["A0"], path))
-            evals += r.force_evals
-            if stats is not None:
-                stats.append(r)
-        return evals
+        if path == "plain":   # the reference GPU path: one tissue at a time
+            rs = [vx.vx_minimize(t, X, p, **opts_for(c["A0"], path))
+                  for c, mesh, p, t, X0, X in cases]
+        else:                 # one persistent launch for the three relaxations
+            rs = vx.vx_minimize_many([cs[3] for cs in cases], [cs[5] for cs in cases],
+                                     [cs[2] for cs in cases], **opts_for(cases[0][0]["A0"], path))
+        if stats is not None:
+            stats.extend(rs)
+        return sum(r.force_evals for r in rs)
 
     def timed(path, steps, warmup):
         for _ in range(warmup):
@@ -240,9 +246,11 @@ def run_gpu(args):
         for k, (c, mesh, p, t, X0, X) in enumerate(cases):
             vx.vx_tissue_restore(t)
             X.copy_(X0h[k], non_blocking=True)
-            r = vx.vx_minimize(t, X, p, **opts_for(c["A0"], "auto"))
-            Xh[k].copy_(X, non_blocking=True)
-            e_evals += r.force_evals
+        rs = vx.vx_minimize_many([cs[3] for cs in cases], [cs[5] for cs in cases],
+                                 [cs[2] for cs in cases], **opts_for(cases[0][0]["A0"], "auto"))
+        for k, cs in enumerate(cases):
+            Xh[k].copy_(cs[5], non_blocking=True)
+        e_evals += sum(r.force_evals for r in rs)
         torch.cuda.synchronize()
         e_ms += 1e3 * (time.perf_counter() - t0)
     e2e = V * e_evals / (e_ms * 1e-3)
@@ -251,18 +259,20 @@ def run_gpu(args):
         dist.all_reduce(t_, op=dist.ReduceOp.SUM)
         e2e = t_.item()
 
-    # roofline of the dominant kernel: one persistent relaxation, event-timed
-    c, mesh, p, t, X0, X = cases[1]
-    vx.vx_tissue_restore(t)
-    X.copy_(X0)
+    # roofline of the dominant kernel: the one persistent launch of a step,
+    # event-timed on the launching stream
+    for c, mesh, p, t, X0, X in cases:
+        vx.vx_tissue_restore(t)
+        X.copy_(X0)
     flush.zero_()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    r = vx.vx_minimize(t, X, p, **opts_for(c["A0"], "auto"))
+    rs = vx.vx_minimize_many([cs[3] for cs in cases], [cs[5] for cs in cases],
+                             [cs[2] for cs in cases], **opts_for(cases[0][0]["A0"], "auto"))
     b.record()
     b.synchronize()
     k_ms = a.elapsed_time(b)
-    bytes_alg = algorithmic_bytes_per_iter(n) * r.force_evals
+    bytes_alg = algorithmic_bytes_per_iter(n) * sum(r.force_evals for r in rs)
     achieved = bytes_alg / (k_ms * 1e-3) / 1e9
     peaks = {}
     try:
@@ -297,10 +307,10 @@ def run_gpu(args):
         "converged": conv,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * V * 16,
                 "d2h_bytes_per_step": 3 * V * 16},
-        "gpu_launches": 3 * args.steps if path_used != 2 else None,
+        "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_min_cluster (one persistent launch per relaxation)",
+                     "kernel": "k_min_cluster_many (one persistent launch, one 16-CTA cluster per relaxation)",
                      "note": "algorithmic bytes/iteration x iterations / launch time; the "
                              "tissue state lives in L2, peak is the measured HBM copy rate"},
         "clocks": clk.summary(),

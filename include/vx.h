@@ -227,6 +227,20 @@ void vx_min_opts_default(vx_min_opts* o);
 vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
                       vx_min_result* r, void* stream);
 
+/*
+ * vx_minimize_many — vx_minimize for several tissues at once: one persistent
+ * launch holds every tissue that fits a CTA's shared memory (one CTA each)
+ * and one holds the others (one 16-CTA cluster each), so independent
+ * relaxations (a parameter sweep, the members of an ensemble) share the GPU
+ * instead of running one after another.  Each tissue gets the same result
+ * as from vx_minimize.  tissues [count], X [count] (dev float64 [V_k][2],
+ * in/out), params [count], r host [count] (out).  Tissues must be distinct,
+ * of one dtype, and fit the resident or cluster path.  Synchronises `stream`.
+ */
+vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
+                           const vx_params* params, const vx_min_opts* o, vx_min_result* r,
+                           void* stream);
+
 /* Outer-gradient options. */
 typedef struct {
   int32_t mode;        /* VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD      */

@@ -19,7 +19,7 @@ from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # 
                     VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
 
 __all__ = ["vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
-           "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "Tissue",
+           "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "vx_minimize_many", "Tissue",
            "Batch", "vx_batch_create", "vx_minimize_batched", "vx_batch_autotune",
            "vx_batch_restore", "EquilibriumFn", "VxError"]
 
@@ -223,6 +223,33 @@ def vx_minimize(t: Tissue, X, params, **opts):
     capi.check(st, "vx_minimize")
     return MinResult(r.status, r.iters, r.n_t1, r.n_stretch, r.n_short_edges, r.n_inverted,
                      r.fmax, r.energy, r.path_used, r.force_evals)
+
+
+def vx_minimize_many(tissues, Xs, params, **opts):
+    """Relax several tissues in one launch (see vx.h).  Xs: list of device
+    f64 [V_k, 2] tensors updated in place; params: one dict per tissue (or
+    one dict for all).  Returns a list of MinResult."""
+    count = len(tissues)
+    if isinstance(params, dict):
+        params = [params] * count
+    for X in Xs:
+        if not (hasattr(X, "is_cuda") and X.is_cuda and X.dtype == _torch().float64
+                and X.is_contiguous()):
+            raise TypeError("every X must be a contiguous float64 CUDA tensor")
+    keep = []
+    parr = (capi.vx_params * count)()
+    for k, (t, p) in enumerate(zip(tissues, params)):
+        prm, kk = make_params(p, t.n, t.E)
+        parr[k] = prm
+        keep.append(kk)
+    hs = (C.c_void_p * count)(*[t.handle.value for t in tissues])
+    xs = (C.c_void_p * count)(*[X.data_ptr() for X in Xs])
+    o = min_opts(**opts)
+    r = (capi.vx_min_result * count)()
+    st = capi.vx_minimize_many(hs, count, xs, parr, C.byref(o), r, _stream())
+    capi.check(st, "vx_minimize_many")
+    return [MinResult(x.status, x.iters, x.n_t1, x.n_stretch, x.n_short_edges, x.n_inverted,
+                      x.fmax, x.energy, x.path_used, x.force_evals) for x in r]
 
 
 @dataclass

@@ -106,6 +106,9 @@ vx_energy_forces = _sig("vx_energy_forces", C.c_int, C.c_void_p, C.c_void_p,
 vx_min_opts_default = _sig("vx_min_opts_default", None, C.POINTER(vx_min_opts))
 vx_minimize = _sig("vx_minimize", C.c_int, C.c_void_p, C.c_void_p, C.POINTER(vx_params),
                    C.POINTER(vx_min_opts), C.POINTER(vx_min_result), C.c_void_p)
+vx_minimize_many = _sig("vx_minimize_many", C.c_int, C.POINTER(C.c_void_p), C.c_int32,
+                        C.POINTER(C.c_void_p), C.POINTER(vx_params), C.POINTER(vx_min_opts),
+                        C.POINTER(vx_min_result), C.c_void_p)
 vx_grad_opts_default = _sig("vx_grad_opts_default", None, C.POINTER(vx_grad_opts))
 vx_equilibrium_grad = _sig("vx_equilibrium_grad", C.c_int, C.c_void_p, C.c_void_p,
                            C.POINTER(vx_params), C.c_void_p, C.POINTER(vx_grad_opts), C.c_void_p,
@@ -132,7 +135,8 @@ vx_batch_autotune = _sig("vx_batch_autotune", C.c_int, C.c_void_p, C.c_void_p,
 EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx_tissue_create",
             "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_tissue_restore",
             "vx_hessian_vector", "vx_energy_forces",
-            "vx_min_opts_default", "vx_minimize", "vx_grad_opts_default", "vx_equilibrium_grad",
+            "vx_min_opts_default", "vx_minimize", "vx_minimize_many", "vx_grad_opts_default",
+            "vx_equilibrium_grad",
             "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
             "vx_batch_topology", "vx_energy_forces_noalloc",
             "vx_minimize_batched", "vx_batch_autotune"]

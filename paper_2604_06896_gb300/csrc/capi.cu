@@ -444,6 +444,42 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
   return (vx_status)out.status == VX_ERR_NONFINITE ? VX_ERR_NONFINITE : VX_OK;
 }
 
+vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
+                           const vx_params* params, const vx_min_opts* o, vx_min_result* r,
+                           void* stream) {
+  if (!tissues || !X || !params || !r || count < 1) return invalid("NULL argument or count < 1");
+  std::string m;
+  if (!min_opts_ok(o, &m)) return invalid(m);
+  std::vector<vx::ParamsD> prms(count);
+  for (int k = 0; k < count; ++k) {
+    if (!tissues[k] || !X[k]) return invalid("NULL tissue or X at " + std::to_string(k));
+    if (!params_ok(&params[k], &m)) return invalid(m);
+    prms[k] = to_params(&params[k]);
+    for (int q = 0; q < k; ++q)
+      if (tissues[q] == tissues[k]) return invalid("a tissue appears twice");
+  }
+  std::vector<vx::MinOut> out(count);
+  std::vector<int> paths(count);
+  const vx_status s = vx::minimize_many(tissues, count, X, prms.data(), to_min_params(o),
+                                        out.data(), paths.data(), as_stream(stream));
+  if (s != VX_OK) return s;
+  vx_status worst = VX_OK;
+  for (int k = 0; k < count; ++k) {
+    r[k].status = out[k].status;
+    r[k].iters = out[k].iters;
+    r[k].n_t1 = out[k].n_t1;
+    r[k].n_stretch = out[k].n_stretch;
+    r[k].n_short_edges = out[k].n_short;
+    r[k].n_inverted = out[k].n_inverted;
+    r[k].fmax = out[k].fmax;
+    r[k].energy = out[k].energy;
+    r[k].path_used = paths[k];
+    r[k].force_evals = out[k].force_evals;
+    if (out[k].status == VX_ERR_NONFINITE) worst = VX_ERR_NONFINITE;
+  }
+  return worst;
+}
+
 void vx_grad_opts_default(vx_grad_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));

@@ -4,6 +4,11 @@
 // adjoint; plus the path choice.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "persistent.cuh"
 #include "tissue.h"
 #include "vx_internal.h"
@@ -195,6 +200,40 @@ __global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
   tm.sync();
 }
 
+// Several tissues in one launch: cluster k (blocks k*NR .. k*NR+NR-1) solves
+// tissue k with the same body as k_min_cluster.
+template <class P, int T, int NR, int MAXC>
+__global__ void __launch_bounds__(T) k_min_cluster_many(const PersistArgs* args) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  __shared__ double slots[3][4 * (T / 32 + 2)];
+  const PersistArgs& g = args[blockIdx.x / NR];
+  ClusterTeam<T, NR> tm;
+  for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
+  for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
+  Slots sl = {slots[0], slots[1], slots[2]};
+  min_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
+                                        g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
+  tm.sync();
+}
+
+// Several resident tissues in one launch: CTA k solves tissue k.
+template <class P, int T, int MAXC>
+__global__ void __launch_bounds__(T) k_min_res_many(const PersistArgs* args) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const PersistArgs& g = args[blockIdx.x];
+  void *cell, *lam, *pvec;
+  uint32_t *sh, *tc;
+  Slots sl;
+  View<P> v = load_resident<P, T>(g, smem, false, &cell, &lam, &pvec, &sh, &tc, &sl);
+  __syncthreads();
+  BlockTeam<T> tm;
+  min_body<P, BlockTeam<T>, MAXC>(tm, v, (R2*)cell, (const typename P::R*)lam, sh, tc, sl, g.prm,
+                                  g.mp, g.Xin, g.Xout, g.out);
+  __syncthreads();
+  store_topology<P, T>(g, v);
+}
+
 template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_adj_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
@@ -364,6 +403,144 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
   if (cudaMemcpyAsync(out, t->dout, sizeof(MinOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error(std::string("vx_minimize: ") + cudaGetErrorString(cudaGetLastError()));
+    return VX_ERR_CUDA;
+  }
+  return VX_OK;
+}
+
+// ------------------------------------------------------- many tissues
+
+namespace {
+std::mutex g_many_mu;
+void* g_many_buf[64] = {};
+size_t g_many_bytes[64] = {};
+
+// A device buffer for the argument and result arrays of vx_minimize_many,
+// grown on demand and kept per device.
+void* many_buffer(size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_many_mu);
+  if (g_many_bytes[dev] < bytes) {
+    if (g_many_buf[dev]) cudaFree(g_many_buf[dev]);
+    g_many_buf[dev] = nullptr;
+    g_many_bytes[dev] = 0;
+    if (cudaMalloc(&g_many_buf[dev], bytes) != cudaSuccess) return nullptr;
+    g_many_bytes[dev] = bytes;
+  }
+  return g_many_buf[dev];
+}
+
+template <class P>
+cudaError_t launch_res_many(const std::vector<vx_tissue_s*>& ts, const PersistArgs* d_args,
+                            cudaStream_t s) {
+  int nmax = 0;
+  size_t smem = 0;
+  for (vx_tissue_s* t : ts) {
+    nmax = std::max(nmax, t->n);
+    smem = std::max(smem, res_bytes<P>(t->n, t->V, t->E, t->HE, kResT, false));
+  }
+  const int mc = (nmax + kResT - 1) / kResT;
+  auto go = [&](auto kernel) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    if (e != cudaSuccess) return e;
+    kernel<<<(int)ts.size(), kResT, smem, s>>>(d_args);
+    return cudaGetLastError();
+  };
+  if (mc <= 1) return go(k_min_res_many<P, kResT, 1>);
+  if (mc <= 2) return go(k_min_res_many<P, kResT, 2>);
+  if (mc <= 3) return go(k_min_res_many<P, kResT, 3>);
+  if (mc <= 4) return go(k_min_res_many<P, kResT, 4>);
+  return go(k_min_res_many<P, kResT, 6>);
+}
+
+template <class P>
+cudaError_t launch_cluster_many(const std::vector<vx_tissue_s*>& ts, const PersistArgs* d_args,
+                                cudaStream_t s) {
+  int nmax = 0;
+  for (vx_tissue_s* t : ts) nmax = std::max(nmax, t->n);
+  const int mc = (nmax + kClusterT * kClusterNR - 1) / (kClusterT * kClusterNR);
+  auto go = [&](auto kernel) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterNR * (unsigned)ts.size(), 1, 1);
+    cfg.blockDim = dim3(kClusterT, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterNR;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, d_args);
+  };
+  if (mc <= 1) return go(k_min_cluster_many<P, kClusterT, kClusterNR, 1>);
+  if (mc <= 2) return go(k_min_cluster_many<P, kClusterT, kClusterNR, 2>);
+  if (mc <= 3) return go(k_min_cluster_many<P, kClusterT, kClusterNR, 3>);
+  return go(k_min_cluster_many<P, kClusterT, kClusterNR, 4>);
+}
+}  // namespace
+
+vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, const ParamsD* prms,
+                        const MinParams& mp, MinOut* outs, int* paths, cudaStream_t s) {
+  const int dtype = ts[0]->dtype;
+  std::vector<vx_tissue_s*> res, clu;
+  std::vector<PersistArgs> ares, aclu;
+  std::vector<int> ires, iclu;
+  for (int k = 0; k < count; ++k) {
+    vx_tissue_s* t = ts[k];
+    if (t->dtype != dtype) {
+      set_error("vx_minimize_many: all tissues must have the same dtype");
+      return VX_ERR_INVALID_ARG;
+    }
+    PersistArgs a = make_args(t, Xs[k], Xs[k], prms[k]);
+    a.mp = mp;
+    if (resident_fits(t, false)) {
+      res.push_back(t);
+      ares.push_back(a);
+      ires.push_back(k);
+      paths[k] = VX_PATH_RESIDENT;
+    } else if (cluster_fits(t)) {
+      clu.push_back(t);
+      aclu.push_back(a);
+      iclu.push_back(k);
+      paths[k] = VX_PATH_CLUSTER;
+    } else {
+      set_error("vx_minimize_many: tissue " + std::to_string(k) + " is too large for the persistent kernels");
+      return VX_ERR_INVALID_ARG;
+    }
+  }
+  const size_t nargs = (size_t)count;
+  unsigned char* buf = (unsigned char*)many_buffer(nargs * (sizeof(PersistArgs) + sizeof(MinOut)) + 256);
+  if (!buf) {
+    set_error("vx_minimize_many: out of device memory for the argument arrays");
+    return VX_ERR_OOM;
+  }
+  PersistArgs* d_args = (PersistArgs*)buf;
+  MinOut* d_out = (MinOut*)(buf + a16(nargs * sizeof(PersistArgs)));
+  // results of tissue k go to d_out[k]
+  for (size_t q = 0; q < ares.size(); ++q) ares[q].out = d_out + ires[q];
+  for (size_t q = 0; q < aclu.size(); ++q) aclu[q].out = d_out + iclu[q];
+  std::vector<PersistArgs> all(ares);
+  all.insert(all.end(), aclu.begin(), aclu.end());
+  cudaError_t e = cudaMemcpyAsync(d_args, all.data(), all.size() * sizeof(PersistArgs),
+                                  cudaMemcpyHostToDevice, s);
+  const bool f64 = dtype == VX_F64;
+  if (e == cudaSuccess && !clu.empty())
+    e = f64 ? launch_cluster_many<PolF64>(clu, d_args + ares.size(), s)
+            : launch_cluster_many<PolF32>(clu, d_args + ares.size(), s);
+  if (e == cudaSuccess && !res.empty())
+    e = f64 ? launch_res_many<PolF64>(res, d_args, s) : launch_res_many<PolF32>(res, d_args, s);
+  if (e == cudaSuccess && mp.l_min > 0)
+    for (vx_tissue_s* t : res)
+      if (e == cudaSuccess) e = rebuild_flat(t, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(outs, d_out, nargs * sizeof(MinOut), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("vx_minimize_many: ") + cudaGetErrorString(e));
     return VX_ERR_CUDA;
   }
   return VX_OK;

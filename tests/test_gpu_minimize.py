@@ -154,3 +154,32 @@ def test_c2_full_size_cluster(vx):
     fo = np.sqrt((Fo * Fo).sum(axis=1)).max()
     print(f"c2: oracle fmax at X_gpu {fo:.2e}")
     assert abs(fo - r.fmax) < 1e-2 * r.fmax + 1e-7 * sA
+
+
+def test_minimize_many_matches_single_calls(vx):
+    """Two large tissues (one cluster each) and two small ones (one CTA each)
+    in one call give exactly what separate vx_minimize calls give."""
+    import torch
+    cs = [vi.small_tissue(n, 84 + k, lam_range=(0.02, 0.1)) for k, n in enumerate((4000, 150, 5000, 90))]
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in cs]
+    params = [{k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")} for c in cs]
+    kw = dict(tol=1e-6, max_iter=3000, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    single = []
+    for m, p in zip(meshes, params):
+        t = vx.Tissue(m, "f32")
+        X = torch.tensor(m["vert"], dtype=torch.float64, device="cuda")
+        r = vx.vx_minimize(t, X, p, **kw)
+        single.append((r, X.cpu().numpy(), t.topology()["he"]))
+        t.close()
+    ts = [vx.Tissue(m, "f32") for m in meshes]
+    Xs = [torch.tensor(m["vert"], dtype=torch.float64, device="cuda") for m in meshes]
+    rs = vx.vx_minimize_many(ts, Xs, params, **kw)
+    for k, (r, (r1, X1, he1)) in enumerate(zip(rs, single)):
+        print(f"tissue {k}: path {r.path_used} iters {r.iters} T1 {r.n_t1}")
+        assert r.path_used == r1.path_used
+        assert (r.iters, r.n_t1, r.n_stretch, r.status) == (r1.iters, r1.n_t1, r1.n_stretch, r1.status)
+        assert np.array_equal(Xs[k].cpu().numpy(), X1)
+        assert np.array_equal(ts[k].topology()["he"], he1)
+    assert {r.path_used for r in rs} == {vx.VX_PATH_RESIDENT, vx.VX_PATH_CLUSTER}
+    for t in ts:
+        t.close()
