@@ -206,6 +206,9 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        # named range: ncu --nvtx --nvtx-include "timed_<path>/" lists the
+        # launches of the timed steps only
+        torch.cuda.nvtx.range_push(f"timed_{path}")
         for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -215,6 +218,7 @@ def run_gpu(args):
             b.record()
             b.synchronize()
             total_ms += a.elapsed_time(b)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -320,39 +324,69 @@ def run_gpu(args):
 
 
 def run_profile(args):
-    """Small fixed-size runs for ncu: the 10,000-cell tissue on the cluster
-    path (capped iterations) and the plain path (capped), and the 100-cell
-    FP64 tissue on the resident path (to convergence)."""
+    """Small fixed-size runs for ncu: the three 10,000-cell relaxations in
+    one multi-tissue launch (capped iterations, on the path --path names),
+    then continued from the state reached (few T1 events left), optionally
+    one relaxation alone, the plain path on one of them (capped), and the
+    100-cell FP64 tissue on the resident path (to convergence)."""
     import torch
 
     import paper_2604_06896_gb300 as vx
-    c = vi.tissue_c2(3.7)
-    order = vx.vx_seed_order(c["seeds"], c["Lx"], c["Ly"]) if args.ordered else np.arange(c["n"])
-    mesh = vx.vx_build_mesh(c["seeds"][order], c["Lx"], c["Ly"])
-    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
-    t = vx.Tissue(mesh, "f32")
-    for path, iters in (("cluster", args.profile_iters), ("plain", args.profile_iters // 10)):
-        for rep in range(2):   # the first call includes module loading
+    ts, Xs, ps, meshes = [], [], [], []
+    for p0 in vi.C2_P0_SWEEP:
+        c = vi.tissue_c2(p0)
+        order = vx.vx_seed_order(c["seeds"], c["Lx"], c["Ly"]) if args.ordered else np.arange(c["n"])
+        mesh = vx.vx_build_mesh(c["seeds"][order], c["Lx"], c["Ly"])
+        ps.append({k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")})
+        ts.append(vx.Tissue(mesh, "f32"))
+        meshes.append(mesh)
+        Xs.append(None)
+    A0 = vi.tissue_c2(3.7)["A0"]
+
+    def reset():
+        for k, t in enumerate(ts):
             vx.vx_tissue_restore(t)
-            X = torch.tensor(mesh["vert"], dtype=torch.float64, device="cuda")
-            o = opts_for(c["A0"], path)
-            o["max_iter"] = iters
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = vx.vx_minimize(t, X, p, **o)
-            dt = time.perf_counter() - t0
-        print(f"{path}: {r.iters} iterations, {r.n_t1} T1, {r.n_stretch} stretches in "
-              f"{dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
-        if path == "cluster":
-            # steady state: continue from the relaxed state (few T1 events left)
-            o["max_iter"] = iters
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = vx.vx_minimize(t, X, p, **o)
-            dt = time.perf_counter() - t0
-            print(f"cluster (continued): {r.iters} iterations, {r.n_t1} T1, {r.n_stretch} "
-                  f"stretches in {dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
-    F, E = vx.vx_energy_forces(t, X, p)
+            Xs[k] = torch.tensor(meshes[k]["vert"], dtype=torch.float64, device="cuda")
+
+    def report(label, rs, dt):
+        it = max(r.iters for r in rs)
+        print(f"{label}: {[r.iters for r in rs]} iterations, {[r.n_t1 for r in rs]} T1, "
+              f"{[r.n_stretch for r in rs]} stretches, fmax {[f'{r.fmax:.2e}' for r in rs]}, "
+              f"status {[r.status for r in rs]} in {dt * 1e3:.1f} ms = "
+              f"{dt / max(1, it) * 1e6:.2f} us/iteration", flush=True)
+
+    o = opts_for(A0, args.path)
+    o["max_iter"] = args.profile_iters
+    for rep in range(2):   # the first call includes module loading
+        reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = vx.vx_minimize_many(ts, Xs, ps, **o)
+        dt = time.perf_counter() - t0
+    report(f"many ({args.path})", rs, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs = vx.vx_minimize_many(ts, Xs, ps, **o)
+    dt = time.perf_counter() - t0
+    report(f"many ({args.path}, continued)", rs, dt)
+    if args.profile_single:
+        reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = vx.vx_minimize(ts[1], Xs[1], ps[1], **o)
+        dt = time.perf_counter() - t0
+        report(f"single ({args.path})", [r], dt)
+    reset()
+    o = opts_for(A0, "plain")
+    o["max_iter"] = args.profile_iters // 10
+    for rep in range(2):
+        vx.vx_tissue_restore(ts[1])
+        X = torch.tensor(meshes[1]["vert"], dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = vx.vx_minimize(ts[1], X, ps[1], **o)
+        dt = time.perf_counter() - t0
+    report("plain", [r], dt)
     c1 = vi.tissue_c1()
     m1 = vx.vx_build_mesh(c1["seeds"], c1["Lx"], c1["Ly"])
     p1 = {k: c1[k] for k in ("KA", "KP", "A0", "P0", "lam")}
@@ -361,7 +395,7 @@ def run_profile(args):
     t0 = time.perf_counter()
     r = vx.vx_minimize(t1, X1, p1, **opts_for(c1["A0"], "resident") | {"tol": 1e-8})
     dt = time.perf_counter() - t0
-    print(f"resident c1: {r.iters} iterations in {dt * 1e3:.1f} ms = {dt / max(1, r.iters) * 1e6:.2f} us/iteration")
+    report("resident c1", [r], dt)
     torch.cuda.synchronize()
 
 
@@ -375,6 +409,9 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
     ap.add_argument("--profile-iters", type=int, default=2000)
     ap.add_argument("--ordered", type=int, default=1, help="profile: Hilbert-ordered seeds")
+    ap.add_argument("--path", default="auto", help="profile: path of the multi-tissue launch")
+    ap.add_argument("--profile-single", type=int, default=0,
+                    help="profile: also one relaxation alone on --path")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

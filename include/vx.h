@@ -75,9 +75,15 @@ enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
  *             memory, synchronised by the hardware cluster barrier (up to
  *             16,384 cells);
  *   PLAIN:    one kernel launch per sub-step, convergence polled by the
- *             host every check_every steps (the reference GPU path).
+ *             host every check_every steps (the reference GPU path);
+ *   GRID:     m co-resident CTAs of a cooperative launch (one per 256
+ *             cells, at most one per SM) hold it in L2-resident global
+ *             memory, synchronised by a bounded-wait barrier in global
+ *             memory (up to 4 x 256 cells per SM).  A barrier wait longer
+ *             than 4 s ends the solve with status VX_ERR_TIMEOUT.
  *   AUTO picks RESIDENT, then CLUSTER, then PLAIN. */
-enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2, VX_PATH_CLUSTER = 3 };
+enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2, VX_PATH_CLUSTER = 3,
+       VX_PATH_GRID = 4 };
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* vx_last_error(void);
@@ -196,7 +202,7 @@ typedef struct {
   int32_t n_min;       /* FIRE N_min                                        */
   double  f_inc, f_dec, alpha0, f_alpha;
   double  l_min;       /* T1 threshold; <= 0 disables T1 checks             */
-  int32_t path;        /* VX_PATH_AUTO / RESIDENT / CLUSTER / PLAIN         */
+  int32_t path;        /* VX_PATH_AUTO / RESIDENT / CLUSTER / PLAIN / GRID  */
   int32_t check_every; /* PLAIN path: host polls convergence every k steps  */
 } vx_min_opts;
 
@@ -208,7 +214,7 @@ typedef struct {
   int32_t n_inverted;  /* cells with A <= 0 at the end                      */
   double  fmax;        /* max_i |F_i| at the returned X                     */
   double  energy;
-  int32_t path_used;   /* VX_PATH_RESIDENT, VX_PATH_CLUSTER or VX_PATH_PLAIN */
+  int32_t path_used;   /* VX_PATH_RESIDENT, _CLUSTER, _PLAIN or _GRID       */
   int32_t force_evals;
 } vx_min_result;
 
@@ -230,12 +236,17 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
 /*
  * vx_minimize_many — vx_minimize for several tissues at once: one persistent
  * launch holds every tissue that fits a CTA's shared memory (one CTA each)
- * and one holds the others (one 16-CTA cluster each), so independent
- * relaxations (a parameter sweep, the members of an ensemble) share the GPU
- * instead of running one after another.  Each tissue gets the same result
- * as from vx_minimize.  tissues [count], X [count] (dev float64 [V_k][2],
- * in/out), params [count], r host [count] (out).  Tissues must be distinct,
- * of one dtype, and fit the resident or cluster path.  Synchronises `stream`.
+ * and one holds the others (one 16-CTA cluster each), or, with o->path =
+ * VX_PATH_GRID, one cooperative launch holds them all, each on a share of
+ * the SMs proportional to its cell count.  Independent relaxations (a
+ * parameter sweep, the members of an ensemble) so share the GPU instead of
+ * running one after another.  Each tissue gets the same result as from
+ * vx_minimize on the path it was given (r[k].path_used).  o->path AUTO
+ * puts small tissues on CTAs and large ones on clusters, CLUSTER puts all
+ * on clusters, RESIDENT requires every tissue to fit a CTA; PLAIN is
+ * rejected.  tissues [count], X [count] (dev float64 [V_k][2], in/out),
+ * params [count], r host [count] (out).  Tissues must be distinct and of
+ * one dtype.  Calls are serialised.  Synchronises `stream`.
  */
 vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
                            const vx_params* params, const vx_min_opts* o, vx_min_result* r,

@@ -16,7 +16,8 @@ import numpy as np
 from . import _capi as capi
 from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # noqa: F401
                     VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
-                    VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_PLAIN, VX_PATH_RESIDENT, VxError)
+                    VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_GRID, VX_PATH_PLAIN, VX_PATH_RESIDENT,
+                    VxError)
 
 __all__ = ["vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
            "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "vx_minimize_many", "Tissue",
@@ -129,7 +130,7 @@ def min_opts(**kw):
             v = {"fire": VX_FIRE, "gd": VX_GD}[v]
         if k == "path" and isinstance(v, str):
             v = {"auto": VX_PATH_AUTO, "resident": VX_PATH_RESIDENT, "plain": VX_PATH_PLAIN,
-                 "cluster": VX_PATH_CLUSTER}[v]
+                 "cluster": VX_PATH_CLUSTER, "grid": VX_PATH_GRID}[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown minimiser option {k}")
         setattr(o, k, v)

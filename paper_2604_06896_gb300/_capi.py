@@ -25,7 +25,7 @@ VX_F64, VX_F32 = 0, 1
 VX_FIRE, VX_GD = 0, 1
 VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD = 0, 1, 2
 VX_COST_NONE, VX_COST_V2V, VX_COST_ANISO = 0, 1, 2
-VX_PATH_AUTO, VX_PATH_RESIDENT, VX_PATH_PLAIN, VX_PATH_CLUSTER = 0, 1, 2, 3
+VX_PATH_AUTO, VX_PATH_RESIDENT, VX_PATH_PLAIN, VX_PATH_CLUSTER, VX_PATH_GRID = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "VX_OK", 1: "VX_NOT_CONVERGED", 2: "VX_ERR_INVALID_ARG",
                 3: "VX_ERR_DEGENERATE_SEEDS", 4: "VX_ERR_CUDA", 5: "VX_ERR_OOM",

@@ -398,7 +398,7 @@ static bool min_opts_ok(const vx_min_opts* o, std::string* m) {
   else if (o->max_iter < 0) *m = "max_iter must be >= 0";
   else if (!(o->dt0 > 0) || !(o->dt_max > 0)) *m = "dt0 and dt_max must be positive";
   else if (!(o->gd_lr > 0)) *m = "gd_lr must be positive";
-  else if (o->path < VX_PATH_AUTO || o->path > VX_PATH_CLUSTER) *m = "unknown path";
+  else if (o->path < VX_PATH_AUTO || o->path > VX_PATH_GRID) *m = "unknown path";
   else return true;
   return false;
 }
@@ -441,7 +441,8 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
   r->energy = out.energy;
   r->path_used = used;
   r->force_evals = out.force_evals;
-  return (vx_status)out.status == VX_ERR_NONFINITE ? VX_ERR_NONFINITE : VX_OK;
+  const vx_status st = (vx_status)out.status;
+  return st == VX_ERR_NONFINITE || st == VX_ERR_TIMEOUT ? st : VX_OK;
 }
 
 vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
@@ -460,7 +461,7 @@ vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
   }
   std::vector<vx::MinOut> out(count);
   std::vector<int> paths(count);
-  const vx_status s = vx::minimize_many(tissues, count, X, prms.data(), to_min_params(o),
+  const vx_status s = vx::minimize_many(tissues, count, X, prms.data(), to_min_params(o), o->path,
                                         out.data(), paths.data(), as_stream(stream));
   if (s != VX_OK) return s;
   vx_status worst = VX_OK;
@@ -475,7 +476,8 @@ vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
     r[k].energy = out[k].energy;
     r[k].path_used = paths[k];
     r[k].force_evals = out[k].force_evals;
-    if (out[k].status == VX_ERR_NONFINITE) worst = VX_ERR_NONFINITE;
+    if (out[k].status == VX_ERR_NONFINITE || out[k].status == VX_ERR_TIMEOUT)
+      worst = (vx_status)out[k].status;
   }
   return worst;
 }

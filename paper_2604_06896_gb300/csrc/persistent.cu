@@ -61,6 +61,8 @@ struct PersistArgs {
   int32_t *vfc, *ccnt;
   uint32_t* ccor;
   int32_t* cedge;
+  // grid variant: CTAs grid_base .. grid_base + grid_m - 1 own the tissue
+  int grid_base, grid_m;
 };
 
 template <class P>
@@ -234,6 +236,29 @@ __global__ void __launch_bounds__(T) k_min_res_many(const PersistArgs* args) {
   store_topology<P, T>(g, v);
 }
 
+// Several tissues in one cooperative launch: tissue k owns the CTAs
+// args[k].grid_base .. + grid_m - 1 (bases ascending), which synchronise
+// through bars[k]; part is the [2][gridDim.x][4] table of partial sums.
+template <class P, int T, int MAXC>
+__global__ void __launch_bounds__(T) k_min_grid(const PersistArgs* args, int count, GridBar* bars,
+                                                double* part) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  __shared__ double slots[3][4 * (T / 32 + 2)];
+  __shared__ GridState gs;
+  int k = 0;
+  while (k + 1 < count && args[k + 1].grid_base <= (int)blockIdx.x) ++k;
+  const PersistArgs& g = args[k];
+  if (threadIdx.x == 0) gs = GridState{bars + k, part, g.grid_base, g.grid_m, (int)gridDim.x, 0, 0};
+  __syncthreads();
+  GridTeam<T> tm{&gs};
+  for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
+  for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
+  Slots sl = {slots[0], slots[1], slots[2]};
+  min_body<P, GridTeam<T>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
+                                 g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
+  tm.sync();
+}
+
 template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_adj_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
@@ -363,6 +388,8 @@ size_t resident_smem_bytes(vx_tissue_s* t) {
                             : res_bytes<PolF32>(t->n, t->V, t->E, t->HE, kResT, false);
 }
 
+bool grid_fits(vx_tissue_s* t);
+
 static int choose_path(vx_tissue_s* t, int path, bool adjoint) {
   if (path == VX_PATH_AUTO) {
     if (resident_fits(t, adjoint)) return VX_PATH_RESIDENT;
@@ -371,6 +398,8 @@ static int choose_path(vx_tissue_s* t, int path, bool adjoint) {
   }
   if (path == VX_PATH_RESIDENT && !resident_fits(t, adjoint)) return -1;
   if (path == VX_PATH_CLUSTER && !cluster_fits(t)) return -1;
+  if (path == VX_PATH_GRID && adjoint) return cluster_fits(t) ? VX_PATH_CLUSTER : -1;
+  if (path == VX_PATH_GRID && !grid_fits(t)) return -1;
   if (path == VX_PATH_PLAIN && adjoint) return VX_PATH_CLUSTER;
   return path;
 }
@@ -383,6 +412,12 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
     return VX_ERR_INVALID_ARG;
   }
   *path_used = p;
+  if (p == VX_PATH_GRID) {
+    vx_tissue_s* ts[1] = {t};
+    double* Xs[1] = {X};
+    int used = 0;
+    return minimize_many(ts, 1, Xs, &prm, mp, VX_PATH_GRID, out, &used, s);
+  }
   const bool f64 = t->dtype == VX_F64;
   if (p == VX_PATH_PLAIN)
     return f64 ? minimize_plain_t<PolF64>(t, X, prm, mp, check_every, out, s)
@@ -412,6 +447,7 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
 
 namespace {
 std::mutex g_many_mu;
+std::mutex g_many_call_mu;
 void* g_many_buf[64] = {};
 size_t g_many_bytes[64] = {};
 
@@ -482,14 +518,84 @@ cudaError_t launch_cluster_many(const std::vector<vx_tissue_s*>& ts, const Persi
   if (mc <= 3) return go(k_min_cluster_many<P, kClusterT, kClusterNR, 3>);
   return go(k_min_cluster_many<P, kClusterT, kClusterNR, 4>);
 }
+
+constexpr int kGridT = 256;
+constexpr int kGridMaxC = 4;
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+// CTAs per tissue on the grid path: one per kGridT cells when the SMs
+// suffice, else shares proportional to those demands (at least one each),
+// at most one CTA per SM in total.  Returns the cells-per-thread bound, or
+// 0 if the tissues do not fit.
+int grid_plan(const std::vector<vx_tissue_s*>& ts, int sms, std::vector<int>* m) {
+  long long demand = 0;
+  m->assign(ts.size(), 1);
+  for (size_t k = 0; k < ts.size(); ++k) {
+    (*m)[k] = (ts[k]->n + kGridT - 1) / kGridT;
+    demand += (*m)[k];
+  }
+  if ((long long)ts.size() > sms) return 0;
+  if (demand > sms) {
+    long long used = 0;
+    for (size_t k = 0; k < ts.size(); ++k) {
+      (*m)[k] = std::max(1, (int)((*m)[k] * (long long)sms / demand));
+      used += (*m)[k];
+    }
+    if (used > sms) return 0;
+  }
+  int mc = 1;
+  for (size_t k = 0; k < ts.size(); ++k)
+    mc = std::max(mc, (ts[k]->n + (*m)[k] * kGridT - 1) / ((*m)[k] * kGridT));
+  return mc <= kGridMaxC ? mc : 0;
+}
+
+template <class P>
+cudaError_t launch_grid_many(int mc, int total, int count, const PersistArgs* d_args, GridBar* bars,
+                             double* part, cudaStream_t s) {
+  auto go = [&](auto kernel) -> cudaError_t {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGridT, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm * sm_count() < total) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)total, 1, 1);
+    cfg.blockDim = dim3(kGridT, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, d_args, count, bars, part);
+  };
+  if (mc <= 1) return go(k_min_grid<P, kGridT, 1>);
+  if (mc <= 2) return go(k_min_grid<P, kGridT, 2>);
+  if (mc <= 3) return go(k_min_grid<P, kGridT, 3>);
+  return go(k_min_grid<P, kGridT, 4>);
+}
 }  // namespace
 
+bool grid_fits(vx_tissue_s* t) {
+  std::vector<int> m;
+  return grid_plan({t}, sm_count(), &m) > 0;
+}
+
 vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, const ParamsD* prms,
-                        const MinParams& mp, MinOut* outs, int* paths, cudaStream_t s) {
+                        const MinParams& mp, int path, MinOut* outs, int* paths, cudaStream_t s) {
   const int dtype = ts[0]->dtype;
-  std::vector<vx_tissue_s*> res, clu;
-  std::vector<PersistArgs> ares, aclu;
-  std::vector<int> ires, iclu;
+  if (path == VX_PATH_PLAIN) {
+    set_error("vx_minimize_many: the plain path takes one tissue at a time (vx_minimize)");
+    return VX_ERR_INVALID_ARG;
+  }
+  std::vector<vx_tissue_s*> res, clu, grd;
+  std::vector<PersistArgs> ares, aclu, agrd;
+  std::vector<int> ires, iclu, igrd;
   for (int k = 0; k < count; ++k) {
     vx_tissue_s* t = ts[k];
     if (t->dtype != dtype) {
@@ -498,37 +604,75 @@ vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, co
     }
     PersistArgs a = make_args(t, Xs[k], Xs[k], prms[k]);
     a.mp = mp;
-    if (resident_fits(t, false)) {
+    if (path == VX_PATH_GRID) {
+      grd.push_back(t);
+      agrd.push_back(a);
+      igrd.push_back(k);
+      paths[k] = VX_PATH_GRID;
+    } else if (path != VX_PATH_CLUSTER && resident_fits(t, false)) {
       res.push_back(t);
       ares.push_back(a);
       ires.push_back(k);
       paths[k] = VX_PATH_RESIDENT;
-    } else if (cluster_fits(t)) {
+    } else if (path != VX_PATH_RESIDENT && cluster_fits(t)) {
       clu.push_back(t);
       aclu.push_back(a);
       iclu.push_back(k);
       paths[k] = VX_PATH_CLUSTER;
     } else {
-      set_error("vx_minimize_many: tissue " + std::to_string(k) + " is too large for the persistent kernels");
+      set_error("vx_minimize_many: tissue " + std::to_string(k) + " does not fit the requested path");
       return VX_ERR_INVALID_ARG;
     }
   }
+  std::vector<int> gm;
+  int gmc = 0, total = 0;
+  if (!grd.empty()) {
+    gmc = grid_plan(grd, sm_count(), &gm);
+    if (gmc == 0) {
+      set_error("vx_minimize_many: the tissues do not fit the grid path (at most one CTA per SM, "
+                "4 x 256 cells per CTA)");
+      return VX_ERR_INVALID_ARG;
+    }
+    for (size_t q = 0; q < agrd.size(); ++q) {
+      agrd[q].grid_base = total;
+      agrd[q].grid_m = gm[q];
+      total += gm[q];
+    }
+  }
+  // One buffer per device holds the argument, result, barrier and partial
+  // sum arrays; calls are serialised so that they never share it.
+  std::lock_guard<std::mutex> call_lock(g_many_call_mu);
   const size_t nargs = (size_t)count;
-  unsigned char* buf = (unsigned char*)many_buffer(nargs * (sizeof(PersistArgs) + sizeof(MinOut)) + 256);
+  const size_t o_out = a16(nargs * sizeof(PersistArgs));
+  const size_t o_bar = o_out + a16(nargs * sizeof(MinOut));
+  const size_t o_part = o_bar + a16(grd.size() * sizeof(GridBar));
+  const size_t bytes = o_part + (size_t)2 * total * 4 * sizeof(double) + 256;
+  unsigned char* buf = (unsigned char*)many_buffer(bytes);
   if (!buf) {
     set_error("vx_minimize_many: out of device memory for the argument arrays");
     return VX_ERR_OOM;
   }
   PersistArgs* d_args = (PersistArgs*)buf;
-  MinOut* d_out = (MinOut*)(buf + a16(nargs * sizeof(PersistArgs)));
+  MinOut* d_out = (MinOut*)(buf + o_out);
+  GridBar* d_bar = (GridBar*)(buf + o_bar);
+  double* d_part = (double*)(buf + o_part);
   // results of tissue k go to d_out[k]
   for (size_t q = 0; q < ares.size(); ++q) ares[q].out = d_out + ires[q];
   for (size_t q = 0; q < aclu.size(); ++q) aclu[q].out = d_out + iclu[q];
+  for (size_t q = 0; q < agrd.size(); ++q) agrd[q].out = d_out + igrd[q];
   std::vector<PersistArgs> all(ares);
   all.insert(all.end(), aclu.begin(), aclu.end());
+  all.insert(all.end(), agrd.begin(), agrd.end());
   cudaError_t e = cudaMemcpyAsync(d_args, all.data(), all.size() * sizeof(PersistArgs),
                                   cudaMemcpyHostToDevice, s);
   const bool f64 = dtype == VX_F64;
+  if (e == cudaSuccess && !grd.empty()) {
+    e = cudaMemsetAsync(d_bar, 0, grd.size() * sizeof(GridBar), s);
+    const PersistArgs* da = d_args + ares.size() + aclu.size();
+    if (e == cudaSuccess)
+      e = f64 ? launch_grid_many<PolF64>(gmc, total, (int)grd.size(), da, d_bar, d_part, s)
+              : launch_grid_many<PolF32>(gmc, total, (int)grd.size(), da, d_bar, d_part, s);
+  }
   if (e == cudaSuccess && !clu.empty())
     e = f64 ? launch_cluster_many<PolF64>(clu, d_args + ares.size(), s)
             : launch_cluster_many<PolF32>(clu, d_args + ares.size(), s);

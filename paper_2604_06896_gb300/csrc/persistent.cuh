@@ -174,6 +174,10 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
       }
     }
     tm.template reduce<4>(red, sl.a, 1);
+    if (tm.failed()) {
+      status = VX_ERR_TIMEOUT;
+      break;
+    }
     fmx = sqrt(red[3]);
     if (!(fmx == fmx) || isinf(fmx)) {
       status = VX_ERR_NONFINITE;

@@ -50,7 +50,7 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
                    int check_every, MinOut* out, int* path_used, cudaStream_t s);
 size_t resident_smem_bytes(vx_tissue_s* t);
 vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, const ParamsD* prms,
-                        const MinParams& mp, MinOut* outs, int* paths, cudaStream_t s);
+                        const MinParams& mp, int path, MinOut* outs, int* paths, cudaStream_t s);
 // Recompute the flat tables from the half-edge tables (after a resident
 // solve rewrote the latter).
 cudaError_t rebuild_flat(vx_tissue_s* t, cudaStream_t s);

@@ -52,7 +52,7 @@ def polish(top, p, A0, tol=1e-11):
     return d, np.sqrt((F * F).sum(axis=1)).max(), r
 
 
-@pytest.mark.parametrize("path", ["resident", "plain", "cluster"])
+@pytest.mark.parametrize("path", ["resident", "plain", "cluster", "grid"])
 def test_c1_fp64_same_trajectory(vx, path):
     c = vi.tissue_c1()
     ref, p = setup(c)
@@ -65,7 +65,7 @@ def test_c1_fp64_same_trajectory(vx, path):
           f"oracle iters {ro.iters} t1 {ro.n_t1} st {ro.n_stretch}")
     assert r.converged and r.fmax < 1e-8
     assert r.path_used == {"resident": vx.VX_PATH_RESIDENT, "plain": vx.VX_PATH_PLAIN,
-                           "cluster": vx.VX_PATH_CLUSTER}[path]
+                           "cluster": vx.VX_PATH_CLUSTER, "grid": vx.VX_PATH_GRID}[path]
     check_half_edge_invariants(top)
     assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
     assert np.array_equal(top["he"], ro.tissue["he"])
@@ -76,7 +76,7 @@ def test_c1_fp64_same_trajectory(vx, path):
     assert np.sqrt((Fo * Fo).sum(axis=1)).max() < 1e-8
 
 
-@pytest.mark.parametrize("path", ["resident", "plain", "cluster"])
+@pytest.mark.parametrize("path", ["resident", "plain", "cluster", "grid"])
 def test_fp32_equilibrium_polish(vx, path):
     c = vi.small_tissue(300, 81, p0=3.7, lam_range=(0.02, 0.1))
     ref, p = setup(c)
@@ -129,21 +129,50 @@ def test_not_converged_status(vx):
     assert r.status == 1 and r.iters == 10
 
 
-def test_c2_full_size_cluster(vx):
+@pytest.mark.parametrize("method,iters,tol_x", [("gd", 1500, 1e-9), ("fire", 300, 1e-8)])
+def test_grid_multi_cta_fp64_same_trajectory(vx, method, iters, tol_x):
+    """A 700-cell FP64 tissue on the grid path (three CTAs, so the barrier,
+    the cross-CTA reductions and the T1 pass of rank 0 on positions that
+    other CTAs wrote are exercised) follows the oracle's iterates with T1
+    on.  Gradient descent has no reduction in its update, so the two stay
+    together over a long run; FIRE mixes with team-wide sums whose rounding
+    order differs from the oracle's, and this still-floppy tissue amplifies
+    such differences, so FIRE is compared over a short run."""
+    c = vi.small_tissue(700, 87, lam_range=(0.02, 0.1))
+    ref, p = setup(c)
+    opts = dict(method=method, gd_lr=3e-3, tol=0.0, max_iter=iters, dt0=0.01, dt_max=0.5,
+                l_min=5e-3)
+    r, top = gpu_relax(vx, ref, p, "f64", path="grid", **opts)
+    o = osolv.MinOpts(method=method, gd_lr=3e-3, tol=0.0, max_iter=iters, dt0=0.01, dt_max=0.5)
+    ro = osolv.relax(ref["vert"], ref, p, o, l_min=5e-3)
+    print(f"grid 700 {method}: gpu iters {r.iters} t1 {r.n_t1} st {r.n_stretch} fmax {r.fmax:.3e}; "
+          f"oracle iters {ro.iters} t1 {ro.n_t1} st {ro.n_stretch}; "
+          f"max dx {np.abs(top['vert'] - ro.X).max():.2e}")
+    assert r.path_used == vx.VX_PATH_GRID
+    assert r.iters == ro.iters == iters
+    check_half_edge_invariants(top)
+    assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
+    assert np.array_equal(top["he"], ro.tissue["he"])
+    assert np.abs(top["vert"] - ro.X).max() < tol_x
+    assert abs(r.energy - omodel.energy(ro.X, ro.tissue, p)) < 1e-9 * abs(r.energy)
+
+
+@pytest.mark.parametrize("path", ["cluster", "grid"])
+def test_c2_full_size(vx, path):
     """The 10,000-cell tissue in the launch configuration the benchmark
-    times (FP32, cluster path, T1 on): a valid topology, energy down, and the
-    oracle's forces at the GPU state agree with the GPU's max |F|.  (The
-    stated tolerance is not reached within the iteration cap: see the
-    design notes.)"""
+    times (FP32, T1 on): a valid topology, energy down, and the oracle's
+    forces at the GPU state agree with the GPU's max |F|.  (The stated
+    tolerance is not reached within the iteration cap: see the design
+    notes.)"""
     c = vi.tissue_c2(3.7)
     ref, p = setup(c)
     sA = np.sqrt(c["A0"])
     E0 = omodel.energy(ref["vert"], ref, p)
     r, top = gpu_relax(vx, ref, p, "f32", tol=1e-6 * sA, max_iter=20000, dt0=0.01,
-                       dt_max=0.5, l_min=5e-3 * sA)
+                       dt_max=0.5, l_min=5e-3 * sA, path=path)
     print(f"c2: status {r.status} iters {r.iters} t1 {r.n_t1} st {r.n_stretch} fmax {r.fmax:.2e} "
           f"path {r.path_used}")
-    assert r.path_used == vx.VX_PATH_CLUSTER
+    assert r.path_used == {"cluster": vx.VX_PATH_CLUSTER, "grid": vx.VX_PATH_GRID}[path]
     check_half_edge_invariants(top)
     g = omodel.geometry(top["vert"], top)
     assert abs(g["A"].sum() - 1.0) < 1e-9
@@ -181,5 +210,34 @@ def test_minimize_many_matches_single_calls(vx):
         assert np.array_equal(Xs[k].cpu().numpy(), X1)
         assert np.array_equal(ts[k].topology()["he"], he1)
     assert {r.path_used for r in rs} == {vx.VX_PATH_RESIDENT, vx.VX_PATH_CLUSTER}
+    for t in ts:
+        t.close()
+
+
+def test_minimize_many_grid_matches_single_calls(vx):
+    """On the grid path, four tissues in one cooperative launch (16, 1, 20
+    and 1 CTAs) give exactly what separate grid-path vx_minimize calls give."""
+    import torch
+    cs = [vi.small_tissue(n, 84 + k, lam_range=(0.02, 0.1)) for k, n in enumerate((4000, 150, 5000, 90))]
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in cs]
+    params = [{k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")} for c in cs]
+    kw = dict(tol=1e-6, max_iter=3000, dt0=0.01, dt_max=0.5, l_min=5e-3, path="grid")
+    single = []
+    for m, p in zip(meshes, params):
+        t = vx.Tissue(m, "f32")
+        X = torch.tensor(m["vert"], dtype=torch.float64, device="cuda")
+        r = vx.vx_minimize(t, X, p, **kw)
+        single.append((r, X.cpu().numpy(), t.topology()["he"]))
+        t.close()
+    ts = [vx.Tissue(m, "f32") for m in meshes]
+    Xs = [torch.tensor(m["vert"], dtype=torch.float64, device="cuda") for m in meshes]
+    rs = vx.vx_minimize_many(ts, Xs, params, **kw)
+    for k, (r, (r1, X1, he1)) in enumerate(zip(rs, single)):
+        print(f"grid tissue {k}: iters {r.iters} T1 {r.n_t1} status {r.status} fmax {r.fmax:.2e}")
+        assert r.path_used == r1.path_used == vx.VX_PATH_GRID
+        assert (r.iters, r.n_t1, r.n_stretch, r.status) == (r1.iters, r1.n_t1, r1.n_stretch, r1.status)
+        assert np.array_equal(Xs[k].cpu().numpy(), X1)
+        assert np.array_equal(ts[k].topology()["he"], he1)
+        check_half_edge_invariants(dict(ts[k].topology(), vert=X1))
     for t in ts:
         t.close()
