@@ -169,7 +169,10 @@ __global__ void k_aniso_grad(View<PolF64> v, const double2* cent, const int* kk,
   }
 }
 
-static bool ensure_work(vx_tissue_s* t, size_t doubles) {
+vx_status adjoint_plain(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
+                        int check_every, AdjOut* out, cudaStream_t s);
+
+bool ensure_work(vx_tissue_s* t, size_t doubles) {
   if (t->work_doubles >= doubles) return true;
   if (t->work) cudaFree(t->work);
   t->work = nullptr;
@@ -227,7 +230,10 @@ vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& p
     ap.g_A0 = g_A0;
     ap.g_P0 = g_P0;
     AdjOut out = {};
-    const vx_status st = adjoint_solve(t, Xstar, prm, ap, o->inner.path, &out, s);
+    // the plain path runs the same CG as one launch per sub-step
+    const vx_status st = o->inner.path == VX_PATH_PLAIN
+                             ? adjoint_plain(t, Xstar, prm, ap, o->inner.check_every, &out, s)
+                             : adjoint_solve(t, Xstar, prm, ap, o->inner.path, &out, s);
     if (aniso_grad) cudaFree(aniso_grad);
     if (st != VX_OK) return st;
     r->status = out.status;

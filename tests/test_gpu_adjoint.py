@@ -56,7 +56,7 @@ def test_hvp_parity(vx, equilibrium):
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-8), ("f32", 1e-4)])
-@pytest.mark.parametrize("path", ["resident", "cluster"])
+@pytest.mark.parametrize("path", ["resident", "cluster", "plain"])
 def test_adjoint_parity(vx, equilibrium, dtype, tol, path):
     c, t, p, X, Xt = equilibrium
     C, G = omodel.cost_v2v(X, Xt, t)
