@@ -279,7 +279,11 @@ void vx_grad_opts_default(vx_grad_opts* o);
  * VX_ADJOINT_CG (Methods, "Implicit differentiation", adjoint form):
  *   solve H lam = Pi grad_X C by conjugate gradients on a Hessian-vector
  *   product (Pi removes the two rigid translations, the null space of H),
- *   then g_theta = -(d^2 E / dX dtheta)^T lam.
+ *   then g_theta = -(d^2 E / dX dtheta)^T lam.  The CG runs in one
+ *   persistent launch (o->inner.path AUTO, RESIDENT, CLUSTER; GRID runs it
+ *   on a cluster), or, with o->inner.path = VX_PATH_PLAIN, as one launch per
+ *   sub-step with FP64 vectors and the status polled every
+ *   o->inner.check_every iterations (the reference GPU path).
  * VX_EP_CENTERED / VX_EP_FORWARD (Methods, "Equilibrium propagation"):
  *   re-minimise E +/- (beta/2) C (or E + beta C and the free X*) from X*,
  *   nudging with the translation-free part of grad_X C, and difference
