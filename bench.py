@@ -156,6 +156,65 @@ def algorithmic_bytes_per_iter(n):
     return 32 * V + 16 * V + 12 * HE + 12 * V + 4 * n + 16 * n
 
 
+def grad_metric(vx, torch, steps, warmup):
+    """Equilibrium-gradient solves/s on the 1,000-cell parameter-inference
+    tissue (FP32): one solve = relax from the target equilibrium under the
+    trial tensions to max|F| < 1e-6 sqrt(A0), then the adjoint gradient of
+    the v2v cost with respect to the 3,000 tensions.  The persistent path
+    (automatic choice: one resident CTA) against the plain path (one launch
+    per sub-step for both the minimiser and the CG), same inputs and
+    tolerances, CUDA events around each solve."""
+    c = vi.tissue_c4()
+    mesh = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
+    base = dict(KA=c["KA"], KP=c["KP"], A0=c["A0"], P0=c["P0"])
+    sA = math.sqrt(c["A0"])
+    t0 = vx.Tissue(mesh, "f32")
+    Xt = torch.tensor(mesh["vert"], dtype=torch.float64, device="cuda")
+    vx.vx_minimize(t0, Xt, dict(base, lam=c["lam_hidden"]), **opts_for(c["A0"], "auto"))
+    top = t0.topology()
+    top["vert"] = Xt.cpu().numpy()
+    t0.close()
+    t = vx.Tissue(top, "f32")     # created at the target's topology: restore returns to it
+    X = torch.empty_like(Xt)
+    p = dict(base, lam=c["lam"])
+    out = {}
+    for path in ("auto", "plain"):
+        o = opts_for(c["A0"], path)
+
+        def solve():
+            vx.vx_tissue_restore(t)
+            X.copy_(Xt)
+            r = vx.vx_minimize(t, X, p, **o)
+            g, rg = vx.vx_equilibrium_grad(t, X, p, cost=vx.VX_COST_V2V, cost_data=Xt,
+                                           cg_rtol=1e-6, inner=dict(path=path))
+            return r, rg
+
+        for _ in range(warmup):
+            solve()
+        torch.cuda.synchronize()
+        ms, rs = 0.0, []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rs.append(solve())
+            b.record()
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        r, rg = rs[-1]
+        out[path] = {"value": steps / (ms * 1e-3), "ms_per_solve": ms / steps,
+                     "path": {1: "resident", 2: "plain", 3: "cluster", 4: "grid"}.get(r.path_used),
+                     "min_status": r.status, "min_iters": r.iters, "n_t1": r.n_t1,
+                     "fmax": r.fmax, "cg_status": rg.status, "cg_iters": rg.cg_iters,
+                     "cg_rel_residual": rg.cg_rel_residual}
+    t.close()
+    return {"metric": "equilibrium-gradient solves/s", "unit": "solves/s",
+            "workload": "c4: 1,000-cell tissue, 3,000 tension parameters, v2v cost; relax to "
+                        "max|F|<1e-6*sqrt(A0) from the target equilibrium, then the adjoint "
+                        "(CG to rtol 1e-6)",
+            "value": out["auto"]["value"], "vs_plain_gpu_path": out["auto"]["value"] / out["plain"]["value"],
+            "persistent": out["auto"], "plain_gpu_path": out["plain"]}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -285,6 +344,8 @@ def run_gpu(args):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
 
+    grad = grad_metric(vx, torch, steps=max(1, args.steps), warmup=1)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_sample(seconds=12.0)
@@ -311,12 +372,15 @@ def run_gpu(args):
         "converged": conv,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * V * 16,
                 "d2h_bytes_per_step": 3 * V * 16},
-        "gpu_launches": args.steps,
+        # per step: one k_rebuild_flat per tissue (vx_tissue_restore) and the
+        # one persistent minimiser launch
+        "gpu_launches": args.steps * (len(cases) + 1),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_min_cluster_many (one persistent launch, one 16-CTA cluster per relaxation)",
                      "note": "algorithmic bytes/iteration x iterations / launch time; the "
                              "tissue state lives in L2, peak is the measured HBM copy rate"},
+        "equilibrium_gradient": grad,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

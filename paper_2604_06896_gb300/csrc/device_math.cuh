@@ -611,10 +611,27 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
   };
-  for (int w = 0; w < nwords; ++w) {
+  // The mask is scanned 128 words at a time (4 per lane, one coalesced
+  // load), and only words found non-zero are visited; once a join has set a
+  // bit further on in the chunk, the rest of the chunk is read word by word.
+  for (int w0 = 0; w0 < nwords; w0 += 128) {
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = w0 + 4 * lane + q;
+      any |= idx < nwords ? __ldcg(&shortbits[idx]) : 0u;
+    }
+    const unsigned nz = __ballot_sync(0xffffffffu, any != 0);
+    bool joined = false;
+    const int wend = w0 + 128 < nwords ? w0 + 128 : nwords;
+  for (int w = w0; w < wend; ++w) {
+    if (!joined && !((nz >> ((w - w0) >> 2)) & 1u)) {
+      w |= 3;  // skip the rest of this lane's group of four words
+      continue;
+    }
     for (;;) {
       __syncwarp();
-      const uint32_t bits = shortbits[w];
+      const uint32_t bits = __ldcg(&shortbits[w]);
       if (!bits) break;
       const int bit = __ffs(bits) - 1;
       __syncwarp();
@@ -751,13 +768,19 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
       }
       __syncwarp();
       // Edges at a or b with a larger id that are now short join this pass.
+      bool join = false;
       if (lane < 6) {
         const int vv = lane < 3 ? a : b;
         const int hh = v.vout[(lane % 3) * v.V + vv];
         const int f = hh >> 1;
-        if (f > e && edge_len_d(v, hh) < lmin) atomicOr(&shortbits[f >> 5], 1u << (f & 31));
+        if (f > e && edge_len_d(v, hh) < lmin) {
+          atomicOr(&shortbits[f >> 5], 1u << (f & 31));
+          join = true;
+        }
       }
+      joined |= __any_sync(0xffffffffu, join);
     }
+  }
   }
   __syncwarp();
 }

@@ -22,6 +22,9 @@ vx_status minimize_plain_t(vx_tissue_s* t, double* X, const ParamsD& prm, const 
 constexpr int kSmemMax = 227 * 1024;
 constexpr int kClusterT = 256;  // 255 registers per thread: no spills
 constexpr int kClusterNR = 16;
+// Cells one T1 pass may change before the team falls back to a full cell
+// pass (four per candidate).
+constexpr int kDirtyCap = 1024;
 
 __host__ __device__ inline size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -193,10 +196,13 @@ template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
   __shared__ double slots[3][4 * (T / 32 + 2)];
+  __shared__ int dirty[kDirtyCap];
   ClusterTeam<T, NR> tm;
   for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
   for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
   Slots sl = {slots[0], slots[1], slots[2]};
+  sl.dirty = dirty;
+  sl.dirty_cap = kDirtyCap;
   min_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
                                         g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
   tm.sync();
@@ -208,11 +214,14 @@ template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_min_cluster_many(const PersistArgs* args) {
   using R2 = typename Vec2Of<typename P::R>::T;
   __shared__ double slots[3][4 * (T / 32 + 2)];
+  __shared__ int dirty[kDirtyCap];
   const PersistArgs& g = args[blockIdx.x / NR];
   ClusterTeam<T, NR> tm;
   for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
   for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
   Slots sl = {slots[0], slots[1], slots[2]};
+  sl.dirty = dirty;
+  sl.dirty_cap = kDirtyCap;
   min_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
                                         g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
   tm.sync();
@@ -244,6 +253,7 @@ __global__ void __launch_bounds__(T) k_min_grid(const PersistArgs* args, int cou
                                                 double* part) {
   using R2 = typename Vec2Of<typename P::R>::T;
   __shared__ double slots[3][4 * (T / 32 + 2)];
+  __shared__ int dirty[kDirtyCap];
   __shared__ GridState gs;
   int k = 0;
   while (k + 1 < count && args[k + 1].grid_base <= (int)blockIdx.x) ++k;
@@ -254,6 +264,8 @@ __global__ void __launch_bounds__(T) k_min_grid(const PersistArgs* args, int cou
   for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
   for (int w = tm.first(); w < (g.V + 31) / 32; w += tm.stride()) g.touched[w] = 0;
   Slots sl = {slots[0], slots[1], slots[2]};
+  sl.dirty = dirty;
+  sl.dirty_cap = kDirtyCap;
   min_body<P, GridTeam<T>, MAXC>(tm, global_view<P>(g), (R2*)g.cell, g.prm.lam, g.shortbits,
                                  g.touched, sl, g.prm, g.mp, g.Xin, g.Xout, g.out);
   tm.sync();

@@ -35,6 +35,10 @@ struct Slots {
   double* a;
   double* b;
   double* c;
+  // cells the T1 pass changed (rank 0's shared memory); without it, a T1
+  // pass is followed by a full cell pass
+  int* dirty = nullptr;
+  int dirty_cap = 0;
 };
 
 // Minimum-image v2v cost gradient at vertex i: (x_i - x_target,i) / N.
@@ -50,6 +54,25 @@ __device__ __forceinline__ void v2v_grad(const View<P>& v, int i, const double* 
 }
 
 // --------------------------------------------------------------- minimiser
+
+// Coefficients (cA, cP) of the listed cells, by the 32 lanes of one warp,
+// with the same arithmetic as the cell pass of min_body: after a T1 pass
+// only the cells around a moved edge change.  Kept out of line so that the
+// solver loop does not carry its registers.
+template <class P, class R2>
+__device__ __noinline__ void refresh_cells(View<P> vw, R2* cell, const ParamsD& prm,
+                                           const int* list, int count) {
+  using R = typename P::R;
+  for (int q = (int)(threadIdx.x & 31); q < count; q += 32) {
+    const int c = list[q];
+    R A, Pp;
+    cell_geometry(vw, c, A, Pp, (R)0, (uint32_t*)nullptr);
+    R2 cc;
+    cc.x = (R)2 * (R)prm.ka(c) * (A - (R)prm.a0(c));
+    cc.y = (R)2 * (R)prm.kp(c) * (Pp - (R)prm.p0(c));
+    cell[c] = cc;
+  }
+}
 
 template <class P, class Team, int MAXC, class LamT>
 __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P::R>::T* cell,
@@ -130,22 +153,33 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     const bool fl = cell_pass(lminR);
     if (mp.l_min > 0) {
       if (tm.sync_or(fl, sl.b)) {
+        bool ovf = false;
         if (tm.rank() == 0 && threadIdx.x < 32) {
           T1Stats s1 = {0, 0, 0};
-          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1);
+          int nd = 0;
+          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1, sl.dirty, sl.dirty_cap,
+                       sl.dirty ? &nd : nullptr);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
+          nd = __shfl_sync(0xffffffffu, nd, 0);
+          ovf = !sl.dirty || nd > sl.dirty_cap;
+          if (!ovf) refresh_cells(vw, cell, prm, sl.dirty, nd);
         }
-        tm.sync();
+        const bool full = tm.sync_or(ovf, sl.c);
+        // The moved vertices restart from rest.  The 32 vertices of a mask
+        // word belong to the 32 lanes of one warp, which clears the word.
 #pragma unroll
         for (int k = 0; k < MAXV; ++k) {
           const int i = f0 + k * st;
-          if (i < V && ((touched[i >> 5] >> (i & 31)) & 1u)) vx[k] = vy[k] = 0;
+          const uint32_t word = i < V ? touched[i >> 5] : 0u;
+          if ((word >> (i & 31)) & 1u) vx[k] = vy[k] = 0;
+          __syncwarp();
+          if ((threadIdx.x & 31) == 0 && word) touched[i >> 5] = 0;
         }
-        tm.sync();
-        for (int w = f0; w < (V + 31) / 32; w += st) touched[w] = 0;
-        cell_pass((R)0);
-        tm.sync();
+        if (full) {
+          cell_pass((R)0);
+          tm.sync();
+        }
       }
     } else {
       tm.sync();
