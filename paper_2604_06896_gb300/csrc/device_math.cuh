@@ -619,7 +619,9 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = w0 + 4 * lane + q;
-      any |= idx < nwords ? __ldcg(&shortbits[idx]) : 0u;
+      // generic loads: the mask lives in shared memory on the resident
+      // path and in global memory on the team paths
+      any |= idx < nwords ? ((volatile const uint32_t*)shortbits)[idx] : 0u;
     }
     const unsigned nz = __ballot_sync(0xffffffffu, any != 0);
     bool joined = false;
@@ -631,7 +633,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
     }
     for (;;) {
       __syncwarp();
-      const uint32_t bits = __ldcg(&shortbits[w]);
+      const uint32_t bits = ((volatile const uint32_t*)shortbits)[w];
       if (!bits) break;
       const int bit = __ffs(bits) - 1;
       __syncwarp();
