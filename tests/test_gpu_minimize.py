@@ -129,7 +129,7 @@ def test_not_converged_status(vx):
     assert r.status == 1 and r.iters == 10
 
 
-@pytest.mark.parametrize("method,iters,tol_x", [("gd", 1500, 1e-9), ("fire", 300, 1e-8)])
+@pytest.mark.parametrize("method,iters,tol_x", [("gd", 1500, 1e-9), ("fire", 100, 1e-9)])
 def test_grid_multi_cta_fp64_same_trajectory(vx, method, iters, tol_x):
     """A 700-cell FP64 tissue on the grid path (three CTAs, so the barrier,
     the cross-CTA reductions and the T1 pass of rank 0 on positions that
@@ -137,7 +137,9 @@ def test_grid_multi_cta_fp64_same_trajectory(vx, method, iters, tol_x):
     on.  Gradient descent has no reduction in its update, so the two stay
     together over a long run; FIRE mixes with team-wide sums whose rounding
     order differs from the oracle's, and this still-floppy tissue amplifies
-    such differences, so FIRE is compared over a short run."""
+    such differences (measured on every path, the one-CTA resident path
+    included: ~1e-11 after 100 iterations, ~1e-8 after 200, ~1e-3 after
+    300), so FIRE is compared over a short run."""
     c = vi.small_tissue(700, 87, lam_range=(0.02, 0.1))
     ref, p = setup(c)
     opts = dict(method=method, gd_lr=3e-3, tol=0.0, max_iter=iters, dt0=0.01, dt_max=0.5,
