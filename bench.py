@@ -159,11 +159,12 @@ def algorithmic_bytes_per_iter(n):
 def grad_metric(vx, torch, steps, warmup):
     """Equilibrium-gradient solves/s on the 1,000-cell parameter-inference
     tissue (FP32): one solve = relax from the target equilibrium under the
-    trial tensions to max|F| < 1e-6 sqrt(A0), then the adjoint gradient of
-    the v2v cost with respect to the 3,000 tensions.  The persistent path
-    (automatic choice: one resident CTA) against the plain path (one launch
-    per sub-step for both the minimiser and the CG), same inputs and
-    tolerances, CUDA events around each solve."""
+    trial tensions to max|F| < 1e-5 sqrt(A0) (FP32 arithmetic stalls near
+    1.5e-6 on this tissue), then the adjoint gradient of the v2v cost with
+    respect to the 3,000 tensions.  The persistent path (automatic choice:
+    a 16-CTA cluster) against the plain path (one launch per sub-step for
+    both the minimiser and the CG), same inputs and tolerances, CUDA events
+    around each solve."""
     c = vi.tissue_c4()
     mesh = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
     base = dict(KA=c["KA"], KP=c["KP"], A0=c["A0"], P0=c["P0"])
@@ -180,6 +181,7 @@ def grad_metric(vx, torch, steps, warmup):
     out = {}
     for path in ("auto", "plain"):
         o = opts_for(c["A0"], path)
+        o["tol"], o["max_iter"] = 1e-5 * sA, 100_000
 
         def solve():
             vx.vx_tissue_restore(t)
@@ -209,7 +211,7 @@ def grad_metric(vx, torch, steps, warmup):
     t.close()
     return {"metric": "equilibrium-gradient solves/s", "unit": "solves/s",
             "workload": "c4: 1,000-cell tissue, 3,000 tension parameters, v2v cost; relax to "
-                        "max|F|<1e-6*sqrt(A0) from the target equilibrium, then the adjoint "
+                        "max|F|<1e-5*sqrt(A0) from the target equilibrium, then the adjoint "
                         "(CG to rtol 1e-6)",
             "value": out["auto"]["value"], "vs_plain_gpu_path": out["auto"]["value"] / out["plain"]["value"],
             "persistent": out["auto"], "plain_gpu_path": out["plain"]}

@@ -81,7 +81,8 @@ enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
  *             memory, synchronised by a bounded-wait barrier in global
  *             memory (up to 4 x 256 cells per SM).  A barrier wait longer
  *             than 4 s ends the solve with status VX_ERR_TIMEOUT.
- *   AUTO picks RESIDENT, then CLUSTER, then PLAIN. */
+ *   AUTO picks RESIDENT for tissues of up to 512 cells that fit, then
+ *   CLUSTER, then PLAIN (vx_minimize_many: RESIDENT whenever it fits). */
 enum { VX_PATH_AUTO = 0, VX_PATH_RESIDENT = 1, VX_PATH_PLAIN = 2, VX_PATH_CLUSTER = 3,
        VX_PATH_GRID = 4 };
 
