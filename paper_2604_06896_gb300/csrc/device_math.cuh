@@ -390,49 +390,6 @@ __device__ double cell_energy_d(const View<P>& v, int c, const ParamsD& prm) {
   return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
 }
 
-// cell_energy_d from the flat corner list (valid while the flat tables
-// match the half-edge tables): the same corners, offsets and operations in
-// the same order, so the same value; the corner words arrive in four 16-byte
-// loads and every position load is issued before the first is used.
-template <class P>
-__device__ double cell_energy_flat_d(const View<P>& v, int c, const ParamsD& prm) {
-  const int m = v.ccnt[c];
-  const uint4* cw = reinterpret_cast<const uint4*>(v.ccor + (size_t)c * kMaxCorners);
-  uint32_t cor[kMaxCorners];
-#pragma unroll
-  for (int q = 0; q < kMaxCorners / 4; ++q) {
-    const uint4 w = cw[q];
-    cor[4 * q] = w.x;
-    cor[4 * q + 1] = w.y;
-    cor[4 * q + 2] = w.z;
-    cor[4 * q + 3] = w.w;
-  }
-  double2 Xc[kMaxCorners];
-#pragma unroll
-  for (int k = 0; k < kMaxCorners; ++k)
-    if (k < m) Xc[k] = P::to_d(v.X[tgt_v(cor[k])]);
-  const double2 X0 = Xc[0];
-  double qx = 0, qy = 0, A2 = 0, pp = 0;
-#pragma unroll
-  for (int k = 1; k <= kMaxCorners; ++k) {
-    if (k > m) break;
-    double nx = 0, ny = 0;
-    if (k < m) {
-      nx = (Xc[k].x + tgt_ox(cor[k]) * v.Lx) - X0.x;
-      ny = (Xc[k].y + tgt_oy(cor[k]) * v.Ly) - X0.y;
-    } else {
-      nx = (X0.x + 0 * v.Lx) - X0.x;
-      ny = (X0.y + 0 * v.Ly) - X0.y;
-    }
-    A2 += qx * ny - nx * qy;
-    pp += sqrt((nx - qx) * (nx - qx) + (ny - qy) * (ny - qy));
-    qx = nx;
-    qy = ny;
-  }
-  const double A = 0.5 * A2, dA = A - prm.a0(c), dP = pp - prm.p0(c);
-  return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
-}
-
 // Rebuild the flat-table entries of vertex w and of cell c from the
 // half-edge tables (after a T1 rewired them).
 template <class P>
@@ -646,10 +603,9 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
   const int lane = threadIdx.x & 31;
   const int nwords = (v.E + 31) >> 5;
   const double lnew = kT1Stretch * lmin;
-  // flat: the flat tables describe the current topology (before a trial)
-  auto local_energy = [&](const int* cells, const int* hes, bool flat) -> double {
+  auto local_energy = [&](const int* cells, const int* hes) -> double {
     double x = 0.0;
-    if (lane < 4) x = flat ? cell_energy_flat_d(v, cells[lane], prm) : cell_energy_d(v, cells[lane], prm);
+    if (lane < 4) x = cell_energy_d(v, cells[lane], prm);
     else if (lane < 9) x = prm.la(hes[lane - 4] >> 1) * edge_len_d(v, hes[lane - 4]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -706,7 +662,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
       const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
       // face sizes of C1, C2, C3, C4 in parallel
       const int fh[4] = {h, hq, ta_p, tb_z};
-      const int fs = lane < 4 ? (v.ccor ? v.ccnt[cells[lane]] : face_size(v, fh[lane])) : 0;
+      const int fs = lane < 4 ? face_size(v, fh[lane]) : 0;
       const int s1 = __shfl_sync(0xffffffffu, fs, 0), s2 = __shfl_sync(0xffffffffu, fs, 1);
       const int s3 = __shfl_sync(0xffffffffu, fs, 2), s4 = __shfl_sync(0xffffffffu, fs, 3);
       const bool allow = s1 > 3 && s2 > 3 && (!v.ccor || (s3 < kMaxCorners && s4 < kMaxCorners)) &&
@@ -729,7 +685,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
         v.X[b] = Xbs;
       }
       __syncwarp();
-      const double Es = local_energy(cells, hes, v.ccor != nullptr);
+      const double Es = local_energy(cells, hes);
       bool take_t1 = false;
       if (allow) {
         const int sv_nxt_i[6] = {hp1, hp2, tx_a, hq, tb_y, h};
@@ -777,7 +733,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
           if (v.ffirst[C2] == hq) v.ffirst[C2] = hn2;
         }
         __syncwarp();
-        const double Et = local_energy(cells, hes, false);
+        const double Et = local_energy(cells, hes);
         take_t1 = Et < Es;
         __syncwarp();
         if (!take_t1 && lane == 0) {
