@@ -378,6 +378,35 @@ vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p,
                             const vx_min_opts* o, int32_t probe_iters, int32_t* threads_out,
                             int32_t* smem_out, void* stream);
 
+/*
+ * vx_equilibrium_grad_batched — the adjoint gradient (Methods, "Implicit
+ * differentiation", adjoint form; as vx_equilibrium_grad with
+ * VX_ADJOINT_CG) for every tissue of the batch in one persistent launch:
+ * CTAs take tissues largest first and run the block-Jacobi preconditioned CG
+ * on each, tissue and CG vectors in L2-resident global memory.  The
+ * topology is the batch's current one (after vx_minimize_batched).
+ * Xstar dev float64 [sum V][2]; dCdX dev float64 [sum V][2] (the outer
+ * cost's gradient, e.g. from vx_batch_aniso_cost); CG stops at
+ * |r| <= cg_rtol |b| or after cg_max_iter iterations; g_lambda dev
+ * [sum E], g_A0, g_P0 dev [sum n], each may be NULL; r host [count] (out).
+ * Returns VX_ERR_INDEFINITE if CG met non-positive curvature in a tissue
+ * (see r[k].status).  Synchronises `stream`.
+ */
+vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_batch_params* p,
+                                      const double* dCdX, double cg_rtol, int32_t cg_max_iter,
+                                      double* g_lambda, double* g_A0, double* g_P0,
+                                      vx_grad_result* r, void* stream);
+
+/*
+ * vx_batch_aniso_cost — the anisotropy cost of every tissue (the batched
+ * inverse-design workload's outer cost; the mean cell-shape tensor Q,
+ * q = ((Qxx - Qyy) / tr Q, 2 Qxy / tr Q), C = |q - q_target|^2) and its
+ * gradient.  X dev float64 [sum V][2]; q_target dev float64 [2]; C host
+ * [count] (out); dCdX dev float64 [sum V][2] (out).  Synchronises `stream`.
+ */
+vx_status vx_batch_aniso_cost(vx_batch b, const double* X, const double* q_target, double* C,
+                              double* dCdX, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # 
                     VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_GRID, VX_PATH_PLAIN, VX_PATH_RESIDENT,
                     VxError)
 
-__all__ = ["vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
+__all__ = ["vx_batch_aniso_cost", "vx_equilibrium_grad_batched", "vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
            "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "vx_minimize_many", "Tissue",
            "Batch", "vx_batch_create", "vx_minimize_batched", "vx_batch_autotune",
            "vx_batch_restore", "EquilibriumFn", "VxError"]
@@ -445,6 +445,42 @@ def vx_minimize_batched(b: Batch, X, params, **opts):
     capi.check(st, "vx_minimize_batched")
     return [MinResult(x.status, x.iters, x.n_t1, x.n_stretch, x.n_short_edges, x.n_inverted,
                       x.fmax, x.energy, x.path_used, x.force_evals) for x in r]
+
+
+def vx_batch_aniso_cost(b: Batch, X, q_target):
+    """Anisotropy cost of every tissue: (host array [count] of C, device f64
+    [sum V, 2] of grad_X C)."""
+    torch = _torch()
+    Vt, Et, nt = int(b.V.sum()), int(b.E.sum()), int(b.n.sum())
+    X = _dev_f64(X, (Vt, 2))
+    qt = _dev_f64(np.asarray(q_target, dtype=np.float64).reshape(2))
+    C_ = np.zeros(b.count, dtype=np.float64)
+    G = torch.empty((Vt, 2), dtype=torch.float64, device="cuda")
+    st = capi.vx_batch_aniso_cost(b.handle, _ptr(X), _ptr(qt), C_.ctypes.data, _ptr(G), _stream())
+    capi.check(st, "vx_batch_aniso_cost")
+    return C_, G
+
+
+def vx_equilibrium_grad_batched(b: Batch, Xstar, params, dCdX, cg_rtol=1e-10, cg_max_iter=20000):
+    """Adjoint gradients of every tissue of the batch at X* (device f64
+    [sum V, 2]) for the outer-cost gradient dCdX (same shape).  Returns
+    (dict of device f64 tensors lam [sum E], A0 [sum n], P0 [sum n], list of
+    GradResult)."""
+    torch = _torch()
+    Vt, Et, nt = int(b.V.sum()), int(b.E.sum()), int(b.n.sum())
+    Xstar = _dev_f64(Xstar, (Vt, 2))
+    dCdX = _dev_f64(dCdX, (Vt, 2))
+    prm, keep = make_batch_params(params, b)
+    g = {k: torch.empty(m, dtype=torch.float64, device="cuda")
+         for k, m in (("lam", Et), ("A0", nt), ("P0", nt))}
+    r = (capi.vx_grad_result * b.count)()
+    st = capi.vx_equilibrium_grad_batched(b.handle, _ptr(Xstar), C.byref(prm), _ptr(dCdX), cg_rtol,
+                                          cg_max_iter, _ptr(g["lam"]), _ptr(g["A0"]),
+                                          _ptr(g["P0"]), r, _stream())
+    if st not in (capi.VX_OK, capi.VX_ERR_INDEFINITE):
+        capi.check(st, "vx_equilibrium_grad_batched")
+    return g, [GradResult(x.status, x.cg_iters, x.cg_rel_residual, x.cost, tuple(x.nudged_iters))
+               for x in r]
 
 
 def vx_batch_autotune(b: Batch, X, params, probe_iters=200, **opts):

@@ -132,6 +132,12 @@ vx_batch_autotune = _sig("vx_batch_autotune", C.c_int, C.c_void_p, C.c_void_p,
                          C.POINTER(vx_batch_params), C.POINTER(vx_min_opts), C.c_int32,
                          P_i32, P_i32, C.c_void_p)
 
+vx_equilibrium_grad_batched = _sig("vx_equilibrium_grad_batched", C.c_int, C.c_void_p, C.c_void_p,
+                                   C.POINTER(vx_batch_params), C.c_void_p, C.c_double, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+vx_batch_aniso_cost = _sig("vx_batch_aniso_cost", C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p, C.c_void_p)
+
 EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx_tissue_create",
             "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology", "vx_tissue_restore",
             "vx_hessian_vector", "vx_energy_forces",
@@ -139,7 +145,8 @@ EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx
             "vx_equilibrium_grad",
             "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
             "vx_batch_topology", "vx_energy_forces_noalloc",
-            "vx_minimize_batched", "vx_batch_autotune"]
+            "vx_minimize_batched", "vx_batch_autotune", "vx_equilibrium_grad_batched",
+            "vx_batch_aniso_cost"]
 
 
 class VxError(RuntimeError):

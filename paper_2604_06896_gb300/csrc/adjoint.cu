@@ -172,6 +172,29 @@ __global__ void k_aniso_grad(View<PolF64> v, const double2* cent, const int* kk,
 vx_status adjoint_plain(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
                         int check_every, AdjOut* out, cudaStream_t s);
 
+size_t aniso_scratch_doubles(int n) { return 3 * (size_t)n + 3 * (size_t)((n + 255) / 256) + 8; }
+
+// The anisotropy cost of one tissue given as an FP64 view (X = positions):
+// C to the host, grad_X C to gradX [V][2] (device).  `scratch` holds
+// aniso_scratch_doubles(n) doubles.  Synchronises s.
+vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double* gradX,
+                          double* scratch, double* C, cudaStream_t s) {
+  const int nb = (v.n + 255) / 256;
+  double2* cent = (double2*)scratch;
+  int* kk = (int*)(scratch + 2 * (size_t)v.n);
+  double* part = scratch + 3 * (size_t)v.n;
+  double* g = part + 3 * (size_t)nb;
+  k_aniso_cells<<<nb, 256, 0, s>>>(v, cent, kk, part);
+  k_aniso_final<<<1, 32, 0, s>>>(part, nb, v.n, q_target, g);
+  k_aniso_grad<<<(v.V + 255) / 256, 256, 0, s>>>(v, cent, kk, g, (double2*)gradX);
+  if (cudaMemcpyAsync(C, g, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error(std::string("anisotropy cost: ") + cudaGetErrorString(cudaGetLastError()));
+    return VX_ERR_CUDA;
+  }
+  return VX_OK;
+}
+
 bool ensure_work(vx_tissue_s* t, size_t doubles) {
   if (t->work_doubles >= doubles) return true;
   if (t->work) cudaFree(t->work);

@@ -52,6 +52,10 @@ struct vx_batch_s {
   // graph cache
   cudaGraphExec_t gexec;
   std::vector<unsigned char> gkey;
+  // batched adjoint: per-cell 4-vectors, CG vectors x, r, p, z, inverse
+  // diagonal blocks (allocated at the first gradient call)
+  void* adj_ws;
+  vx::AdjOut* d_adj_out;
 };
 
 namespace vx {
@@ -184,6 +188,93 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
     }
     __syncthreads();
   }
+}
+
+struct BatchAdjArgs {
+  const BatchDesc* desc;
+  const int* order;
+  int* counter;
+  int count;
+  const double* X;     // X* [V_tot][2]
+  const double* dCdX;  // [V_tot][2]
+  uint32_t* tgt;
+  int32_t *nxt, *face, *vout, *ffirst;
+  void *Xw, *cell4, *x, *r, *p, *z, *pre;
+  const double *KA, *KP, *A0, *P0, *lam;
+  double rtol;
+  int max_iter;
+  double *g_lam, *g_A0, *g_P0;  // [E_tot], [n_tot], [n_tot] or null
+  AdjOut* out;
+};
+
+// The implicit adjoint for many tissues: every CTA takes tissues from the
+// largest-first queue and runs adj_body_mem on each, tissue and CG vectors
+// in L2-resident global memory.
+template <class P, int T>
+__global__ void __launch_bounds__(T) k_adj_batch(BatchAdjArgs g) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  using R4 = typename Vec2Of<R>::T4;
+  __shared__ int item;
+  __shared__ double slots[3][4 * (T / 32 + 1)];
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(g.counter, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= g.count) break;
+    const BatchDesc d = g.desc[g.order[k]];
+    ParamsD prm;
+    prm.KA = g.KA ? g.KA + d.cbase : nullptr;
+    prm.KP = g.KP ? g.KP + d.cbase : nullptr;
+    prm.A0 = g.A0 ? g.A0 + d.cbase : nullptr;
+    prm.P0 = g.P0 ? g.P0 + d.cbase : nullptr;
+    prm.lam = g.lam ? g.lam + d.ebase : nullptr;
+    prm.KA_s = d.KA;
+    prm.KP_s = d.KP;
+    prm.A0_s = d.A0;
+    prm.P0_s = d.P0;
+    prm.lam_s = d.lam;
+    View<P> v;
+    v.vnb = nullptr;
+    v.vfc = nullptr;
+    v.ccnt = nullptr;
+    v.ccor = nullptr;
+    v.cedge = nullptr;
+    v.n = d.n;
+    v.V = d.V;
+    v.E = d.E;
+    v.box = P::make_box(d.Lx, d.Ly);
+    v.Lx = d.Lx;
+    v.Ly = d.Ly;
+    v.X = (typename P::Pos*)g.Xw + d.vbase;
+    v.tgt = g.tgt + d.hbase;
+    v.nxt = g.nxt + d.hbase;
+    v.face = g.face + d.hbase;
+    v.vout = g.vout + 3 * d.vbase;
+    v.ffirst = g.ffirst + d.cbase;
+    Slots sl = {slots[0], slots[1], slots[2]};
+    adj_body_mem<P, T>(v, (R4*)g.cell4 + d.cbase, (R2*)g.x + d.vbase, (R2*)g.r + d.vbase,
+                       (R2*)g.p + d.vbase, (R2*)g.z + d.vbase, (R4*)g.pre + d.vbase, prm.lam, sl,
+                       prm, g.dCdX + 2 * (size_t)d.vbase, g.rtol, g.max_iter,
+                       g.X + 2 * (size_t)d.vbase, g.g_lam ? g.g_lam + d.ebase : nullptr,
+                       g.g_A0 ? g.g_A0 + d.cbase : nullptr, g.g_P0 ? g.g_P0 + d.cbase : nullptr,
+                       g.out + g.order[k]);
+    __syncthreads();
+  }
+}
+
+template <class P>
+static cudaError_t launch_adj_batch(const BatchAdjArgs& a, int count, cudaStream_t s) {
+  constexpr int T = 256;
+  int occ = 0, dev = 0, sms = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_batch<P, T>, T, 0);
+  if (e != cudaSuccess) return e;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(count, occ * sms));
+  k_adj_batch<P, T><<<grid, T, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <class P, int T>
@@ -367,7 +458,8 @@ vx_status vx_batch_destroy(vx_batch b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   void* ptrs[] = {b->d_desc, b->d_order, b->d_counter, b->tgt,  b->nxt,   b->face,  b->vout,
                   b->ffirst, b->tgt0,    b->nxt0,      b->face0, b->vout0, b->ffirst0, b->Xw,
-                  b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out};
+                  b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out,
+                  b->adj_ws, b->d_adj_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -648,6 +740,124 @@ vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p, con
   if (threads_out) *threads_out = bt;
   if (smem_out) *smem_out = bs;
   return cudaStreamSynchronize(s) == cudaSuccess ? VX_OK : fail(VX_ERR_CUDA, "autotune");
+}
+
+vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_batch_params* p,
+                                      const double* dCdX, double cg_rtol, int32_t cg_max_iter,
+                                      double* g_lambda, double* g_A0, double* g_P0,
+                                      vx_grad_result* r, void* stream) {
+  if (!b || !Xstar || !p || !dCdX || !r) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  if (!(cg_rtol >= 0) || cg_max_iter < 0) return fail(VX_ERR_INVALID_ARG, "invalid CG options");
+  cudaStream_t s = (cudaStream_t)stream;
+  set_tissue_params(b, p);
+  if (cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(VX_ERR_CUDA, "descriptor upload");
+  const size_t rs = b->dtype == VX_F64 ? 8 : 4;  // bytes of one real
+  auto r256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_x = r256(4 * rs * (size_t)b->n_tot);
+  const size_t vec = r256(2 * rs * (size_t)b->V_tot);
+  const size_t o_pre = o_x + 4 * vec;
+  const size_t bytes = o_pre + r256(4 * rs * (size_t)b->V_tot);
+  if (!b->adj_ws && cudaMalloc(&b->adj_ws, bytes) != cudaSuccess) {
+    b->adj_ws = nullptr;
+    return fail(VX_ERR_OOM, "out of device memory for the batched adjoint");
+  }
+  if (!b->d_adj_out && cudaMalloc((void**)&b->d_adj_out, sizeof(vx::AdjOut) * b->count) != cudaSuccess) {
+    b->d_adj_out = nullptr;
+    return fail(VX_ERR_OOM, "out of device memory for the batched adjoint");
+  }
+  unsigned char* w = (unsigned char*)b->adj_ws;
+  vx::BatchAdjArgs a = {};
+  a.desc = b->d_desc;
+  a.order = b->d_order;
+  a.counter = b->d_counter;
+  a.count = b->count;
+  a.X = Xstar;
+  a.dCdX = dCdX;
+  a.tgt = b->tgt;
+  a.nxt = b->nxt;
+  a.face = b->face;
+  a.vout = b->vout;
+  a.ffirst = b->ffirst;
+  a.Xw = b->Xw;
+  a.cell4 = w;
+  a.x = w + o_x;
+  a.r = w + o_x + vec;
+  a.p = w + o_x + 2 * vec;
+  a.z = w + o_x + 3 * vec;
+  a.pre = w + o_pre;
+  a.KA = p->KA;
+  a.KP = p->KP;
+  a.A0 = p->A0;
+  a.P0 = p->P0;
+  a.lam = p->lambda;
+  a.rtol = cg_rtol;
+  a.max_iter = cg_max_iter;
+  a.g_lam = g_lambda;
+  a.g_A0 = g_A0;
+  a.g_P0 = g_P0;
+  a.out = b->d_adj_out;
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4, s);
+  if (e == cudaSuccess)
+    e = b->dtype == VX_F64 ? vx::launch_adj_batch<vx::PolF64>(a, b->count, s)
+                           : vx::launch_adj_batch<vx::PolF32>(a, b->count, s);
+  std::vector<vx::AdjOut> out(b->count);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out.data(), b->d_adj_out, sizeof(vx::AdjOut) * b->count,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess)
+    return fail(VX_ERR_CUDA, std::string("vx_equilibrium_grad_batched: ") + cudaGetErrorString(e));
+  vx_status worst = VX_OK;
+  for (int k = 0; k < b->count; ++k) {
+    r[k].status = out[k].status;
+    r[k].cg_iters = out[k].iters;
+    r[k].cg_rel_residual = out[k].rel_residual;
+    r[k].cost = 0.0;
+    r[k].nudged_iters[0] = r[k].nudged_iters[1] = 0;
+    if (out[k].status == VX_ERR_INDEFINITE || out[k].status == VX_ERR_NONFINITE)
+      worst = (vx_status)out[k].status;
+  }
+  if (worst == VX_ERR_INDEFINITE)
+    set_error("CG met a direction of non-positive curvature in at least one tissue");
+  return worst;
+}
+
+vx_status vx_batch_aniso_cost(vx_batch b, const double* X, const double* q_target, double* C,
+                              double* dCdX, void* stream) {
+  if (!b || !X || !q_target || !C || !dCdX) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int nmax = 0;
+  for (const BatchDesc& d : b->desc) nmax = std::max(nmax, d.n);
+  double* scratch = nullptr;
+  if (cudaMalloc(&scratch, 8 * vx::aniso_scratch_doubles(nmax)) != cudaSuccess)
+    return fail(VX_ERR_OOM, "out of device memory for the anisotropy cost");
+  vx_status st = VX_OK;
+  for (int k = 0; k < b->count && st == VX_OK; ++k) {
+    const BatchDesc& d = b->desc[k];
+    vx::View<vx::PolF64> v;
+    v.X = (double2*)(X + 2 * (size_t)d.vbase);
+    v.tgt = b->tgt + d.hbase;
+    v.nxt = b->nxt + d.hbase;
+    v.face = b->face + d.hbase;
+    v.vout = b->vout + 3 * (size_t)d.vbase;
+    v.ffirst = b->ffirst + d.cbase;
+    v.n = d.n;
+    v.V = d.V;
+    v.E = d.E;
+    v.box = vx::PolF64::make_box(d.Lx, d.Ly);
+    v.Lx = d.Lx;
+    v.Ly = d.Ly;
+    v.vnb = nullptr;
+    v.vfc = nullptr;
+    v.ccnt = nullptr;
+    v.ccor = nullptr;
+    v.cedge = nullptr;
+    st = vx::aniso_cost_view(v, q_target, dCdX + 2 * (size_t)d.vbase, scratch, &C[k], s);
+  }
+  cudaFree(scratch);
+  return st;
 }
 
 }  // extern "C"

@@ -885,4 +885,186 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     }
 }
 
+// ------------------------------------------------- adjoint, memory state
+
+// The implicit adjoint of adj_body for one CTA, with the CG vectors (x, r,
+// p, z) and the inverse diagonal blocks in arrays instead of registers, so
+// that one kernel serves tissues of any size (the batched path).  The right
+// side grad_X C comes in dCdX; the same preconditioned CG, stop rule and
+// parameter VJP as adj_body.
+template <class P, int T, class LamT>
+__device__ void adj_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T4* cell4,
+                             typename Vec2Of<typename P::R>::T* x,
+                             typename Vec2Of<typename P::R>::T* r,
+                             typename Vec2Of<typename P::R>::T* p,
+                             typename Vec2Of<typename P::R>::T* z,
+                             typename Vec2Of<typename P::R>::T4* pre, const LamT* lam, Slots sl,
+                             const ParamsD& prm, const double* dCdX, double rtol, int max_iter,
+                             const double* Xin, double* g_lam, double* g_A0, double* g_P0,
+                             AdjOut* out) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  using R4 = typename Vec2Of<R>::T4;
+  BlockTeam<T> tm;
+  const int n = vw.n, V = vw.V, E = vw.E, tid = threadIdx.x;
+  if (Xin)
+    for (int i = tid; i < V; i += T) vw.X[i] = P::from_d(Xin[2 * i], Xin[2 * i + 1]);
+  tm.sync();
+  for (int c = tid; c < n; c += T) {
+    R A, Pp;
+    cell_geometry(vw, c, A, Pp, (R)0, nullptr);
+    R4 q;
+    q.x = (R)(2.0 * prm.ka(c) * ((double)A - prm.a0(c)));
+    q.y = (R)(2.0 * prm.kp(c) * ((double)Pp - prm.p0(c)));
+    q.z = (R)(2.0 * prm.ka(c));
+    q.w = (R)(2.0 * prm.kp(c));
+    cell4[c] = q;
+  }
+  tm.sync();
+  double s2[2] = {0, 0};
+  for (int i = tid; i < V; i += T) {
+    double dxx, dxy, dyy;
+    vertex_diag(vw, i, cell4, lam, prm.lam_s, dxx, dxy, dyy);
+    const double det = dxx * dyy - dxy * dxy;
+    R4 q;
+    if (dxx > 0 && det > 1e-300 * dxx * dxx) {
+      q.x = (R)(dyy / det);
+      q.y = (R)(-dxy / det);
+      q.z = (R)(dxx / det);
+    } else {
+      const double tr = fabs(dxx) + fabs(dyy);
+      q.x = q.z = (R)(tr > 0 ? 2.0 / tr : 1.0);
+      q.y = 0;
+    }
+    q.w = 0;
+    pre[i] = q;
+    const double gx = dCdX[2 * i], gy = dCdX[2 * i + 1];
+    R2 g;
+    g.x = (R)gx;
+    g.y = (R)gy;
+    r[i] = g;
+    s2[0] += gx;
+    s2[1] += gy;
+  }
+  tm.template reduce<2>(s2, sl.a, 0);
+  const R mx = (R)(s2[0] / V), my = (R)(s2[1] / V);
+  double s2a[2] = {0, 0};  // r.z, r.r
+  for (int i = tid; i < V; i += T) {
+    R2 ri = r[i];
+    ri.x -= mx;
+    ri.y -= my;
+    r[i] = ri;
+    const R4 q = pre[i];
+    R2 zi;
+    zi.x = q.x * ri.x + q.y * ri.y;
+    zi.y = q.y * ri.x + q.z * ri.y;
+    p[i] = zi;
+    R2 zero;
+    zero.x = 0;
+    zero.y = 0;
+    x[i] = zero;
+    s2a[0] += (double)(ri.x * zi.x + ri.y * zi.y);
+    s2a[1] += (double)(ri.x * ri.x + ri.y * ri.y);
+  }
+  tm.template reduce<2>(s2a, sl.b, 0);
+  double rz = s2a[0];
+  const double bnorm = sqrt(s2a[1]);
+  double rnorm = bnorm;
+  int status = VX_NOT_CONVERGED, it = 0;
+  if (bnorm == 0.0) status = VX_OK;
+  tm.sync();
+  for (it = 0; status == VX_NOT_CONVERGED && it < max_iter; ++it) {
+    for (int c = tid; c < n; c += T) {
+      R sA, sP;
+      cell_dir(vw, c, p, sA, sP);
+      R4 q = cell4[c];
+      q.z = (R)(2.0 * prm.ka(c)) * sA;
+      q.w = (R)(2.0 * prm.kp(c)) * sP;
+      cell4[c] = q;
+    }
+    tm.sync();
+    double s1[1] = {0};
+    for (int i = tid; i < V; i += T) {
+      R hx, hy;
+      vertex_hvp(vw, i, cell4, lam, prm.lam_s, p, hx, hy);
+      R2 h;
+      h.x = hx;
+      h.y = hy;
+      z[i] = h;  // H p, until the update below replaces it by M r
+      const R2 pi = p[i];
+      s1[0] += (double)(pi.x * hx + pi.y * hy);
+    }
+    tm.template reduce<1>(s1, sl.a, 0);
+    if (!(s1[0] > 0)) {
+      status = VX_ERR_INDEFINITE;
+      break;
+    }
+    const R al = (R)(rz / s1[0]);
+    double s2b[2] = {0, 0};
+    for (int i = tid; i < V; i += T) {
+      const R2 pi = p[i], hi = z[i];
+      R2 xi = x[i], ri = r[i];
+      xi.x += al * pi.x;
+      xi.y += al * pi.y;
+      ri.x -= al * hi.x;
+      ri.y -= al * hi.y;
+      x[i] = xi;
+      r[i] = ri;
+      const R4 q = pre[i];
+      R2 zi;
+      zi.x = q.x * ri.x + q.y * ri.y;
+      zi.y = q.y * ri.x + q.z * ri.y;
+      z[i] = zi;
+      s2b[0] += (double)(ri.x * zi.x + ri.y * zi.y);
+      s2b[1] += (double)(ri.x * ri.x + ri.y * ri.y);
+    }
+    tm.template reduce<2>(s2b, sl.b, 0);
+    rnorm = sqrt(s2b[1]);
+    if (!(rnorm == rnorm)) {
+      status = VX_ERR_NONFINITE;
+      break;
+    }
+    if (rnorm <= rtol * bnorm) status = VX_OK;
+    const R be = (R)(s2b[0] / rz);
+    rz = s2b[0];
+    if (status == VX_NOT_CONVERGED)
+      for (int i = tid; i < V; i += T) {
+        const R2 zi = z[i];
+        R2 pi = p[i];
+        pi.x = zi.x + be * pi.x;
+        pi.y = zi.y + be * pi.y;
+        p[i] = pi;
+      }
+    tm.sync();
+  }
+  tm.sync();
+  // g = -(d^2E / dX dtheta)^T lambda with lambda = x.
+  if (g_lam)
+    for (int e = tid; e < E; e += T) {
+      const int h = 2 * e;
+      const uint32_t tg = vw.tgt[h];
+      const int s = src_of(vw, h), t = tgt_v(tg);
+      R dx, dy;
+      P::diff(vw.X[t], vw.X[s], tgt_ox(tg), tgt_oy(tg), vw.box, dx, dy);
+      const R il = P::rsqrt(dx * dx + dy * dy);
+      const R2 lt = x[t], ls = x[s];
+      g_lam[e] = -(double)((dx * (lt.x - ls.x) + dy * (lt.y - ls.y)) * il);
+    }
+  if (g_A0 || g_P0)
+    for (int c = tid; c < n; c += T) {
+      R sA, sP;
+      cell_dir(vw, c, x, sA, sP);
+      if (g_A0) g_A0[c] = 2.0 * prm.ka(c) * (double)sA;
+      if (g_P0) g_P0[c] = 2.0 * prm.kp(c) * (double)sP;
+    }
+  if (tid == 0 && out) {
+    AdjOut o;
+    o.status = status;
+    o.iters = it;
+    o.rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+    o.cost = 0.0;
+    *out = o;
+  }
+}
+
 }  // namespace vx

@@ -59,4 +59,7 @@ vx_status hessian_vector(vx_tissue_s* t, const double* X, const ParamsD& prm, co
 vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
                            const double* dCdX, const vx_grad_opts* o, double* g_lambda, double* g_A0,
                            double* g_P0, vx_grad_result* r, cudaStream_t s);
+size_t aniso_scratch_doubles(int n);
+vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double* gradX,
+                          double* scratch, double* C, cudaStream_t s);
 }  // namespace vx
