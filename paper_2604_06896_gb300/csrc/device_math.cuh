@@ -589,12 +589,6 @@ __device__ __noinline__ void t1_pass(View<P> v, const ParamsD& prm, double lmin,
   }
 }
 
-// Hint: bring the line holding p into this SM's L1 (generic address of
-// global memory).
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.L1 [%0];" ::"l"(p));
-}
-
 // Warp-cooperative form of t1_pass: the same decisions in the same order,
 // executed by the 32 lanes of one warp.  Lane 0 does the bookkeeping and the
 // writes; lanes 0..3 evaluate the four cells and lanes 4..8 the five edges of
@@ -666,32 +660,6 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
       const int kxx = tgt_ox(v.tgt[hn2]), kxy = tgt_oy(v.tgt[hn2]);
       const int kyx = kbx + tgt_ox(v.tgt[hn1]), kyy = kby + tgt_oy(v.tgt[hn1]);
       const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
-      // Everything the candidate will read lies in the four cells: with the
-      // flat tables the lanes request it all at once (corner positions and
-      // out-lists, half-edge targets, successors and faces) so that the
-      // dependent walks below hit L1 instead of going to L2 one step at a
-      // time.  Prefetches are hints; nothing is read from them.
-      if (v.ccor) {
-        const int c = cells[lane >> 3];
-        const int m = v.ccnt[c];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int k = 2 * (lane & 7) + j;
-          const int hh = v.cedge[(size_t)c * kMaxCorners + k];
-          const uint32_t cw = v.ccor[(size_t)c * kMaxCorners + k];
-          if (k < m) {
-            const int w = tgt_v(cw);
-            prefetch_l1(&v.nxt[hh]);
-            prefetch_l1(&v.tgt[hh]);
-            prefetch_l1(&v.tgt[hh ^ 1]);
-            prefetch_l1(&v.face[hh]);
-            prefetch_l1(&v.X[w]);
-            prefetch_l1(&v.vout[w]);
-            prefetch_l1(&v.vout[v.V + w]);
-            prefetch_l1(&v.vout[2 * v.V + w]);
-          }
-        }
-      }
       // face sizes of C1, C2, C3, C4 in parallel
       const int fh[4] = {h, hq, ta_p, tb_z};
       const int fs = lane < 4 ? face_size(v, fh[lane]) : 0;
