@@ -33,6 +33,8 @@ UNIT = "vertex-force evals/s"
 WORKLOAD = "c2: 10,000-cell periodic Voronoi tissue, FIRE+T1 to max|F|<1e-6*sqrt(A0), p0 in {3.5,3.7,3.9}"
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu
+TRAFFIC_BYTES = 10_298_880 + 111_872
 MAX_ITER = 20_000   # per relaxation; see the design notes on c2's convergence
 
 
@@ -378,10 +380,14 @@ def run_gpu(args):
         # one persistent minimiser launch
         "gpu_launches": args.steps * (len(cases) + 1),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES,
                      "kernel": "k_min_cluster_many (one persistent launch, one 16-CTA cluster per relaxation)",
                      "note": "algorithmic bytes/iteration x iterations / launch time; the "
-                             "tissue state lives in L2, peak is the measured HBM copy rate"},
+                             "tissue state lives in L2, peak is the measured HBM copy rate; "
+                             "traffic = dram bytes read+written by one ncu capture of this "
+                             "kernel (300 iterations of the same three tissues): the state "
+                             "is loaded into L2 once, so it does not grow with iterations "
+                             "(profiles/k_min_cluster_many_c2.md)"},
         "equilibrium_gradient": grad,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
