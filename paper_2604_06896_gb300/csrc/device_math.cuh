@@ -16,6 +16,7 @@
 // Internal half-edge numbering: edge e owns half-edges 2e and 2e + 1 (twin =
 // h ^ 1), 2e being the one with the smaller index in the caller's table.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -390,6 +391,38 @@ __device__ double cell_energy_d(const View<P>& v, int c, const ParamsD& prm) {
   return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
 }
 
+// Local energies of the T1 comparison in the tissue's precision: FP64
+// tissues use the FP64 walks above; FP32 tissues take areas, perimeters and
+// lengths in FP32 from TwoSum-exact local differences (as the cell and
+// force passes do) and only combine them in FP64.  GB300 issues FP64 at a
+// small fraction of the FP32 rate, and a T1 candidate evaluates eight cell
+// energies and ten edge lengths.  The half-edge tables are walked (the flat
+// tables are stale during a trial).
+template <class P>
+__device__ double cell_energy_p(const View<P>& v, int c, const ParamsD& prm) {
+  if constexpr (std::is_same<typename P::R, double>::value) {
+    return cell_energy_d(v, c, prm);
+  } else {
+    View<P> w = v;
+    w.ccor = nullptr;
+    float A, Pp;
+    cell_geometry(w, c, A, Pp, 0.0f, (uint32_t*)nullptr);
+    const double dA = (double)A - prm.a0(c), dP = (double)Pp - prm.p0(c);
+    return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
+  }
+}
+template <class P>
+__device__ __forceinline__ double edge_len_p(const View<P>& v, int h) {
+  if constexpr (std::is_same<typename P::R, double>::value) {
+    return edge_len_d(v, h);
+  } else {
+    const uint32_t tg = v.tgt[h];
+    float dx, dy;
+    P::diff(v.X[tgt_v(tg)], v.X[src_of(v, h)], tgt_ox(tg), tgt_oy(tg), v.box, dx, dy);
+    return (double)sqrtf(dx * dx + dy * dy);
+  }
+}
+
 // Rebuild the flat-table entries of vertex w and of cell c from the
 // half-edge tables (after a T1 rewired them).
 template <class P>
@@ -605,8 +638,8 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
   const double lnew = kT1Stretch * lmin;
   auto local_energy = [&](const int* cells, const int* hes) -> double {
     double x = 0.0;
-    if (lane < 4) x = cell_energy_d(v, cells[lane], prm);
-    else if (lane < 9) x = prm.la(hes[lane - 4] >> 1) * edge_len_d(v, hes[lane - 4]);
+    if (lane < 4) x = cell_energy_p(v, cells[lane], prm);
+    else if (lane < 9) x = prm.la(hes[lane - 4] >> 1) * edge_len_p(v, hes[lane - 4]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
@@ -641,7 +674,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
       __syncwarp();
       const int e = (w << 5) + bit;
       const int h = 2 * e, hq = h ^ 1;
-      if (edge_len_d(v, h) >= lmin) continue;
+      if (edge_len_p(v, h) >= lmin) continue;
       const int a = src_of(v, h), b = tgt_v(v.tgt[h]);
       if (lane == 0) {
         touched[a >> 5] |= 1u << (a & 31);
@@ -775,7 +808,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
         const int vv = lane < 3 ? a : b;
         const int hh = v.vout[(lane % 3) * v.V + vv];
         const int f = hh >> 1;
-        if (f > e && edge_len_d(v, hh) < lmin) {
+        if (f > e && edge_len_p(v, hh) < lmin) {
           atomicOr(&shortbits[f >> 5], 1u << (f & 31));
           join = true;
         }
