@@ -10,6 +10,7 @@
 // CG direction live wherever the View points (shared memory for a resident
 // CTA, L2-resident global memory for a cluster).
 #pragma once
+#include <type_traits>
 #include "device_math.cuh"
 #include "kernels.cuh"
 #include "team.cuh"
@@ -92,16 +93,6 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
       const int i = f0 + k * st;
       if (i < V) vw.X[i] = P::from_d(Xin[2 * i], Xin[2 * i + 1]);
     }
-  R ka[MAXC], kp[MAXC], a0[MAXC], p0[MAXC];
-#pragma unroll
-  for (int k = 0; k < MAXC; ++k) {
-    const int c = f0 + k * st;
-    const int cc = c < n ? c : 0;
-    ka[k] = (R)prm.ka(cc);
-    kp[k] = (R)prm.kp(cc);
-    a0[k] = (R)prm.a0(cc);
-    p0[k] = (R)prm.p0(cc);
-  }
   R vx[MAXV], vy[MAXV], fx[MAXV], fy[MAXV];
 #pragma unroll
   for (int k = 0; k < MAXV; ++k) vx[k] = vy[k] = fx[k] = fy[k] = 0;
@@ -141,8 +132,9 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
         R A, Pp;
         fl |= cell_geometry(vw, c, A, Pp, lm, shortbits);
         R2 cc;
-        cc.x = (R)2 * ka[k] * (A - a0[k]);
-        cc.y = (R)2 * kp[k] * (Pp - p0[k]);
+        // per-cell parameters are read where used (no registers held)
+        cc.x = (R)2 * (R)prm.ka(c) * (A - (R)prm.a0(c));
+        cc.y = (R)2 * (R)prm.kp(c) * (Pp - (R)prm.p0(c));
         cell[c] = cc;
       }
     }
@@ -184,7 +176,11 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     } else {
       tm.sync();
     }
-    double red[4] = {0, 0, 0, 0};  // F.F, F.v, v.v, max |F_i|^2
+    // F.F, F.v, v.v, max |F_i|^2: FP32 tissues sum their per-thread and
+    // per-warp parts in FP32 and combine warps in FP64
+    constexpr bool kF32 = std::is_same<R, float>::value;
+    double red[4] = {0, 0, 0, 0};
+    float redf[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < MAXV; ++k) {
       const int i = f0 + k * st;
@@ -200,20 +196,31 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
           fx[k] -= (R)(mp.nudge_s * (gx - nmx));
           fy[k] -= (R)(mp.nudge_s * (gy - nmy));
         }
-        const double f2 = (double)(fx[k] * fx[k] + fy[k] * fy[k]);
-        red[0] += f2;
-        red[1] += (double)(fx[k] * vx[k] + fy[k] * vy[k]);
-        red[2] += (double)(vx[k] * vx[k] + vy[k] * vy[k]);
-        red[3] = fmax(red[3], f2);
+        if constexpr (kF32) {
+          const float f2 = fx[k] * fx[k] + fy[k] * fy[k];
+          redf[0] += f2;
+          redf[1] += fx[k] * vx[k] + fy[k] * vy[k];
+          redf[2] += vx[k] * vx[k] + vy[k] * vy[k];
+          redf[3] = fmaxf(redf[3], f2);
+        } else {
+          const double f2 = (double)(fx[k] * fx[k] + fy[k] * fy[k]);
+          red[0] += f2;
+          red[1] += (double)(fx[k] * vx[k] + fy[k] * vy[k]);
+          red[2] += (double)(vx[k] * vx[k] + vy[k] * vy[k]);
+          red[3] = fmax(red[3], f2);
+        }
       }
     }
-    tm.template reduce<4>(red, sl.a, 1);
+    if constexpr (kF32)
+      tm.template reduce_f<4>(redf, red, sl.a, 1);
+    else
+      tm.template reduce<4>(red, sl.a, 1);
     if (tm.failed()) {
       status = VX_ERR_TIMEOUT;
       break;
     }
-    fmx = sqrt(red[3]);
-    if (!(fmx == fmx) || isinf(fmx)) {
+    fmx = kF32 ? (double)sqrtf((float)red[3]) : sqrt(red[3]);
+    if (!(fmx == fmx) || isinf(fmx) || !(red[0] == red[0])) {
       status = VX_ERR_NONFINITE;
       break;
     }
@@ -238,7 +245,7 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
       bool zero;
       if (red[1] > 0) {
         mA = (R)(1.0 - alpha);
-        mB = (R)(alpha * sqrt(red[2]) / sqrt(red[0]));
+        mB = (R)alpha * sqrt((R)red[2]) / sqrt((R)red[0]);
         zero = false;
         if (npos > mp.n_min) {
           dt = fmin(dt * mp.f_inc, mp.dt_max);

@@ -28,6 +28,22 @@
 namespace vx {
 namespace cg = cooperative_groups;
 
+// Warp totals of NV FP32 values (sum, or max for the last nmax), fixed
+// shuffle tree, converted to FP64.
+template <int NV>
+__device__ __forceinline__ void warp_tree_f(const float (&v)[NV], double (&out)[NV], int nmax) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = (k >= NV - nmax) ? fmaxf(x, y) : x + y;
+    }
+    out[k] = (double)x;
+  }
+}
+
 template <int T>
 struct BlockTeam {
   static constexpr int kThreads = T;
@@ -43,17 +59,27 @@ struct BlockTeam {
   // Sum (and max in slot MAXK if want_max) of NV values over the team.
   // `slots` holds kWarps * NV doubles; the caller must separate two uses of
   // the same slots by a team barrier.
+  // FP32 values: the warp stage in FP32 (FP64 issues slowly on this GPU),
+  // the team stage in FP64 as in reduce().
   template <int NV>
+  __device__ __forceinline__ void reduce_f(const float (&v)[NV], double (&out)[NV], double* slots,
+                                           int nmax) const {
+    warp_tree_f<NV>(v, out, nmax);
+    reduce<NV, true>(out, slots, nmax);
+  }
+  // kTreeDone: v already holds warp totals (in every lane).
+  template <int NV, bool kTreeDone = false>
   __device__ __forceinline__ void reduce(double (&v)[NV], double* slots, int nmax) const {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double x = v[k];
+      if (!kTreeDone)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(0xffffffffu, x, o);
-        x = (k >= NV - nmax) ? fmax(x, y) : x + y;
-      }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = (k >= NV - nmax) ? fmax(x, y) : x + y;
+        }
       if (lane == 0) slots[w * NV + k] = x;
     }
     __syncthreads();
@@ -82,22 +108,33 @@ struct ClusterTeam {
   __device__ __forceinline__ bool failed() const { return false; }
   // Team-wide OR; uses `slots` like reduce().
   __device__ __forceinline__ bool sync_or(bool p, double* slots) const {
-    double v[1] = {p ? 1.0 : 0.0};
-    reduce<1>(v, slots, 1);
+    const float f[1] = {p ? 1.0f : 0.0f};
+    double v[1];
+    reduce_f<1>(f, v, slots, 1);
     return v[0] > 0.0;
   }
   // `slots` holds (kWarps + 2) * NV doubles.
+  // FP32 values: the warp stage in FP32 (FP64 issues slowly on this GPU),
+  // the team stage in FP64 as in reduce().
   template <int NV>
+  __device__ __forceinline__ void reduce_f(const float (&v)[NV], double (&out)[NV], double* slots,
+                                           int nmax) const {
+    warp_tree_f<NV>(v, out, nmax);
+    reduce<NV, true>(out, slots, nmax);
+  }
+  // kTreeDone: v already holds warp totals (in every lane).
+  template <int NV, bool kTreeDone = false>
   __device__ __forceinline__ void reduce(double (&v)[NV], double* slots, int nmax) const {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double x = v[k];
+      if (!kTreeDone)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(0xffffffffu, x, o);
-        x = (k >= NV - nmax) ? fmax(x, y) : x + y;
-      }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = (k >= NV - nmax) ? fmax(x, y) : x + y;
+        }
       if (lane == 0) slots[w * NV + k] = x;
     }
     __syncthreads();
@@ -222,26 +259,37 @@ struct GridTeam {
     __syncthreads();
   }
   __device__ __forceinline__ bool sync_or(bool p, double* slots) const {
-    double v[1] = {p ? 1.0 : 0.0};
-    reduce<1>(v, slots, 1);
+    const float f[1] = {p ? 1.0f : 0.0f};
+    double v[1];
+    reduce_f<1>(f, v, slots, 1);
     return v[0] > 0.0;
   }
   // `slots` holds (kWarps + 2) * NV doubles, NV <= 4.  Two consecutive
   // reduces use the two halves of `part`; a third may reuse the first half
   // because every CTA has passed the second one's barrier, after its reads
   // of the first.
+  // FP32 values: the warp stage in FP32 (FP64 issues slowly on this GPU),
+  // the team stage in FP64 as in reduce().
   template <int NV>
+  __device__ __forceinline__ void reduce_f(const float (&v)[NV], double (&out)[NV], double* slots,
+                                           int nmax) const {
+    warp_tree_f<NV>(v, out, nmax);
+    reduce<NV, true>(out, slots, nmax);
+  }
+  // kTreeDone: v already holds warp totals (in every lane).
+  template <int NV, bool kTreeDone = false>
   __device__ __forceinline__ void reduce(double (&v)[NV], double* slots, int nmax) const {
     static_assert(NV <= 4, "at most 4 values per reduction");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double x = v[k];
+      if (!kTreeDone)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(0xffffffffu, x, o);
-        x = (k >= NV - nmax) ? fmax(x, y) : x + y;
-      }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = (k >= NV - nmax) ? fmax(x, y) : x + y;
+        }
       if (lane == 0) slots[w * NV + k] = x;
     }
     __syncthreads();
