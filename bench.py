@@ -33,8 +33,9 @@ UNIT = "vertex-force evals/s"
 WORKLOAD = "c2: 10,000-cell periodic Voronoi tissue, FIRE+T1 to max|F|<1e-6*sqrt(A0), p0 in {3.5,3.7,3.9}"
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu
-TRAFFIC_BYTES = 10_298_880 + 111_872
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an
+# ncu capture of the current kernel (None until one is taken)
+TRAFFIC_BYTES = None
 MAX_ITER = 20_000   # per relaxation; see the design notes on c2's convergence
 
 
