@@ -26,6 +26,10 @@ b -> y = next(h) in C1, z -> b = prev(h') in C2, a -> x = next(h') in C2,
 C3 = the third cell at a, C4 = the third cell at b.  After the T1, a sits on
 C1's side, joined to p and y; b on C2's side, joined to x and z; the new edge
 a - b separates C3 from C4.
+
+``wrap`` is the bookkeeping of Methods, "Periodic mode": every vertex is put
+back into the primary box [0, Lx) x [0, Ly) and the offsets of the half-edges
+are changed so that every unwrapped edge vector stays what it was.
 """
 from __future__ import annotations
 
@@ -179,3 +183,39 @@ def t1_pass(X, t, p, l_min):
             if f > e and edge_length(X, t, hh) < l_min:
                 pending.add(f)
     return X, t, touched, n_t1, n_st
+
+
+def wrap_coordinate(x, L):
+    """(x', k) with x' = x - k L in [0, L] and k an integer: k = floor(x / L),
+    corrected by one period when the rounding of x / L or of x - k L left x'
+    outside [0, L); a result that rounds to L is taken as 0."""
+    k = np.floor(x / L)
+    xw = x - k * L
+    hi = xw >= L
+    xw = np.where(hi, xw - L, xw)
+    k = np.where(hi, k + 1, k)
+    lo = xw < 0
+    xw = np.where(lo, xw + L, xw)
+    k = np.where(lo, k - 1, k)
+    xw = np.where(xw >= L, 0.0, xw)
+    return xw, k.astype(np.int64)
+
+
+def wrap(X, t):
+    """Wrap the vertices into the primary box and fix the offsets (Methods,
+    "Periodic mode").  A vertex moved by -k_v L; a half-edge s -> t then
+    needs the offset off + k_t - k_s for X[t] + off L - X[s] to keep its
+    value.  Returns (X', tissue copy)."""
+    he = t["he"].copy()
+    Xw = np.empty_like(X)
+    k = np.zeros(X.shape, dtype=np.int64)
+    for c, L in ((0, t["Lx"]), (1, t["Ly"])):
+        Xw[:, c], k[:, c] = wrap_coordinate(X[:, c], L)
+    src, tgt = he[:, HE_SRC], he[:, HE_TGT]
+    he[:, HE_OFFX] = he[:, HE_OFFX] + k[tgt, 0] - k[src, 0]
+    he[:, HE_OFFY] = he[:, HE_OFFY] + k[tgt, 1] - k[src, 1]
+    tn = dict(t)
+    tn["he"] = he
+    for key in ("_kcorner", "_faces", "_rep"):
+        tn.pop(key, None)
+    return Xw, tn
