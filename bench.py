@@ -36,7 +36,7 @@ WORKLOAD = "c2: 10,000-cell periodic Voronoi tissue, FIRE+T1 to max|F|<1e-6*sqrt
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an
 # ncu capture of the current kernel
 TRAFFIC_BYTES = 10_277_120 + 105_472
-MAX_ITER = 20_000   # per relaxation; see the design notes on c2's convergence
+MAX_ITER = 20_000   # per relaxation: a fixed budget (the tolerance is not reached)
 
 
 def opts_for(A0, path):

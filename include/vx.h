@@ -205,6 +205,12 @@ typedef struct {
   double  l_min;       /* T1 threshold; <= 0 disables T1 checks             */
   int32_t path;        /* VX_PATH_AUTO / RESIDENT / CLUSTER / PLAIN / GRID  */
   int32_t check_every; /* PLAIN path: host polls convergence every k steps  */
+  int32_t wrap;        /* 1 (default): on return every vertex is wrapped into
+                          the box and the offsets fixed (Methods, "Periodic
+                          mode"); 0: positions are left unwrapped          */
+  int32_t* edge_events;/* dev int32 [E][2] or NULL: per edge, the number of
+                          stretches ([e][0]) and T1s ([e][1]) the T1 passes
+                          made are added (a diagnostic of repeated events) */
 } vx_min_opts;
 
 typedef struct {
@@ -228,8 +234,12 @@ void vx_min_opts_default(vx_min_opts* o);
  * max_i |F_i| < tol for `patience` consecutive iterations, or max_iter.
  * Each iteration first checks the edges for T1 transitions (Methods, "T1
  * transitions"; both candidates at length 1.5 l_min, lower energy kept).
- * X dev float64 [V][2], in/out; positions stay unwrapped (the offsets are
- * kept consistent).  r host (out).  Synchronises `stream`.
+ * X dev float64 [V][2], in/out.  Inside the solve positions are unwrapped
+ * and the offsets fixed; with o->wrap (the default) every vertex is then
+ * put back into [0, Lx) x [0, Ly) and the tissue's offsets are changed so
+ * that every unwrapped edge vector keeps its value (an offset that would
+ * leave {-1, 0, 1} gives VX_ERR_TOPOLOGY).  r host (out).  Synchronises
+ * `stream`.
  */
 vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
                       vx_min_result* r, void* stream);
@@ -261,7 +271,12 @@ typedef struct {
   int32_t cg_max_iter;
   int32_t cost;        /* built-in cost for EP (and for adjoint if dCdX NULL) */
   const double* cost_data; /* dev: X_target [V][2] (v2v) or q_target [2]     */
-  vx_min_opts inner;   /* nudged phases (T1 is not applied in them)          */
+  vx_min_opts inner;   /* nudged phases (T1 is not applied in them, nor the
+                          exit-time wrap)                                   */
+  int32_t ep_f64;      /* EP on an FP32 tissue: 1 runs the nudged phases in
+                          FP64 arithmetic (the estimate divides a difference
+                          of two equilibria by beta, so their force balance
+                          must be finer than FP32 forces allow); default 0 */
 } vx_grad_opts;
 
 typedef struct {
@@ -288,7 +303,9 @@ void vx_grad_opts_default(vx_grad_opts* o);
  * VX_EP_CENTERED / VX_EP_FORWARD (Methods, "Equilibrium propagation"):
  *   re-minimise E +/- (beta/2) C (or E + beta C and the free X*) from X*,
  *   nudging with the translation-free part of grad_X C, and difference
- *   d_theta E over beta.
+ *   d_theta E over beta.  The built-in cost is VX_COST_V2V or
+ *   VX_COST_ANISO (its gradient is recomputed from the cells' shapes at
+ *   every iteration of the nudged phases).
  * Xstar dev float64 [V][2]; dCdX dev float64 [V][2] (adjoint; NULL uses the
  * built-in cost).  g_lambda dev [E], g_A0 dev [n], g_P0 dev [n], each may be
  * NULL.  r host (out).  Synchronises `stream`.
@@ -297,6 +314,32 @@ vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params*
                               const double* dCdX, const vx_grad_opts* o,
                               double* g_lambda, double* g_A0, double* g_P0,
                               vx_grad_result* r, void* stream);
+
+/*
+ * Asynchronous forms, for CUDA graphs.  Every call above that takes a
+ * vx_tissue allocates nothing (the workspace is sized by vx_tissue_create);
+ * these two also never synchronise: everything is enqueued on `stream` and
+ * the GPU writes the result struct into r, which is device memory or pinned
+ * (page-locked) host memory, when the work is done.  So they can be
+ * recorded in a CUDA graph and replayed; arguments are checked when the
+ * call is made, the statuses in r describe the run.
+ *
+ * vx_minimize_async — vx_minimize on the persistent paths (o->path AUTO,
+ *   RESIDENT or CLUSTER; AUTO must resolve to one of them); PLAIN and GRID
+ *   are rejected (they poll the host or stage arguments through it).
+ *   r->status is VX_OK, VX_NOT_CONVERGED, VX_ERR_NONFINITE or
+ *   VX_ERR_TOPOLOGY.
+ * vx_equilibrium_grad_async — vx_equilibrium_grad with the persistent
+ *   adjoint or the persistent nudged phases (o->inner.path not PLAIN or
+ *   GRID); r->status as in the synchronous form (VX_ERR_INDEFINITE when CG
+ *   met non-positive curvature).
+ */
+vx_status vx_minimize_async(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
+                            vx_min_result* r, void* stream);
+vx_status vx_equilibrium_grad_async(vx_tissue t, const double* Xstar, const vx_params* p,
+                                    const double* dCdX, const vx_grad_opts* o,
+                                    double* g_lambda, double* g_A0, double* g_P0,
+                                    vx_grad_result* r, void* stream);
 
 /*
  * vx_energy_forces_noalloc — vx_energy_forces for callers that cannot
@@ -309,11 +352,15 @@ vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params*
  * own device memory, the topology tables in the format of this header
  * (he int32 [6n][8], face_he int32 [n], edge_id int32 [6n]), X float64
  * [2n][2], and the outputs F float64 [2n][2] (or NULL) and E float64 [1] (or
- * NULL), plus status int32 [1], set to 1 when a vertex is not 3-valent.
- * Arithmetic is FP64.  Nothing is allocated and no allocating library routine
- * is called: the kernels' scratch lives in one static device array sized for
- * at most 32,768 cells (about 1.8 MB, held by every GPU that loads the
- * library until the process exits); larger tissues are rejected with
+ * NULL), plus status int32 [1], which every call clears and then sets to
+ * the OR of: 1 when a vertex is not the source of exactly three half-edges
+ * (that vertex gets no force), 2 when a table holds an index out of range
+ * (the access is skipped; F and E are then not meaningful).  Both checks run
+ * whether or not F is asked for.  Arithmetic is FP64.  Nothing is allocated
+ * and no allocating library routine is called: the kernels' scratch lives in
+ * one static device array sized for at most 32,768 cells (196,864 doubles =
+ * 1,574,912 bytes, about 1.5 MiB, held by every GPU that loads the library
+ * until the process exits); larger tissues are rejected with
  * VX_ERR_INVALID_ARG.  The first call on a device looks up the array's
  * device address (with that device current) and caches it: make that first
  * call before any stream capture.  All calls share the one array: calls
@@ -324,6 +371,24 @@ vx_status vx_energy_forces_noalloc(const int32_t* he, const int32_t* face_he,
                                    const int32_t* edge_id, int32_t n_cells, double Lx, double Ly,
                                    const double* X, const vx_params* p, double* F, double* E,
                                    int32_t* status, void* stream);
+
+/*
+ * vx_grid_barrier_selftest — exercises the bounded wait of the GRID path's
+ * barrier without a fault (the paper has no counterpart: this checks the
+ * library's failure detection).  One cooperative launch of `ctas`
+ * co-resident CTAs passes `rounds` barriers with the same barrier code the
+ * GRID minimiser uses, each wait limited to wait_s seconds (0 < wait_s
+ * <= 10).  The CTA of rank absent_rank (or none, when it is negative)
+ * leaves before the first barrier, so the others' waits run out.
+ * status host int32 [ctas] (out): VX_OK for a CTA that passed every
+ * barrier, VX_ERR_TIMEOUT for one whose wait ran out (or that saw another
+ * CTA's time-out), -1 for the absent CTA.  Returns VX_ERR_TIMEOUT if any
+ * CTA timed out, VX_ERR_INVALID_ARG if the CTAs cannot all be resident.
+ * Allocates a few bytes of device memory for the barrier; synchronises
+ * `stream`.
+ */
+vx_status vx_grid_barrier_selftest(int32_t ctas, int32_t absent_rank, int32_t rounds,
+                                   double wait_s, int32_t* status, void* stream);
 
 /* ------------------------------------------------------------ batches */
 

@@ -131,6 +131,8 @@ def min_opts(**kw):
         if k == "path" and isinstance(v, str):
             v = {"auto": VX_PATH_AUTO, "resident": VX_PATH_RESIDENT, "plain": VX_PATH_PLAIN,
                  "cluster": VX_PATH_CLUSTER, "grid": VX_PATH_GRID}[v]
+        if k == "edge_events" and v is not None and hasattr(v, "data_ptr"):
+            v = v.data_ptr()    # a device int32 [E, 2] tensor
         if not hasattr(o, k):
             raise TypeError(f"unknown minimiser option {k}")
         setattr(o, k, v)
@@ -226,6 +228,75 @@ def vx_minimize(t: Tissue, X, params, **opts):
                      r.fmax, r.energy, r.path_used, r.force_evals)
 
 
+def result_buffer(kind="min", pinned=False):
+    """A buffer for the result struct of vx_minimize_async (kind "min") or
+    vx_equilibrium_grad_async ("grad"): a uint8 tensor on the device, or in
+    pinned host memory."""
+    torch = _torch()
+    n = C.sizeof(capi.vx_min_result if kind == "min" else capi.vx_grad_result)
+    if pinned:
+        return torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+    return torch.zeros(n, dtype=torch.uint8, device="cuda")
+
+
+def read_result(buf, kind="min"):
+    """The MinResult / GradResult held in a result_buffer (synchronises)."""
+    torch = _torch()
+    torch.cuda.synchronize()
+    raw = bytes(buf.cpu().numpy().tobytes())
+    if kind == "min":
+        x = capi.vx_min_result.from_buffer_copy(raw)
+        return MinResult(x.status, x.iters, x.n_t1, x.n_stretch, x.n_short_edges, x.n_inverted,
+                         x.fmax, x.energy, x.path_used, x.force_evals)
+    x = capi.vx_grad_result.from_buffer_copy(raw)
+    return GradResult(x.status, x.cg_iters, x.cg_rel_residual, x.cost, tuple(x.nudged_iters))
+
+
+class Params:
+    """vx_params built once (device copies kept alive), for calls that are
+    recorded in a CUDA graph."""
+
+    def __init__(self, t, p):
+        self.struct, self.keep = make_params(p, t.n, t.E)
+
+
+def vx_minimize_async(t: Tissue, X, params, result, **opts):
+    """vx_minimize without host synchronisation (see vx.h): the GPU writes
+    the result into `result` (a result_buffer("min")).  params: a dict or a
+    Params (use Params inside a CUDA graph capture)."""
+    prm = params if isinstance(params, Params) else Params(t, params)
+    o = min_opts(**opts)
+    st = capi.vx_minimize_async(t.handle, _ptr(X), C.byref(prm.struct), C.byref(o),
+                                C.c_void_p(result.data_ptr()), _stream())
+    capi.check(st, "vx_minimize_async")
+    return prm
+
+
+def vx_equilibrium_grad_async(t: Tissue, Xstar, params, g, result, dCdX=None, mode=VX_ADJOINT_CG,
+                              beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, cost=VX_COST_NONE,
+                              cost_data=None, inner=None, ep_f64=0):
+    """vx_equilibrium_grad without host synchronisation (see vx.h): the
+    gradients go to the device tensors g["lam"], g["A0"], g["P0"] (each may
+    be missing) and the GPU writes the result into `result` (a
+    result_buffer("grad")).  Xstar, dCdX and cost_data must be device
+    float64 tensors already (nothing is copied)."""
+    prm = params if isinstance(params, Params) else Params(t, params)
+    o = capi.vx_grad_opts()
+    capi.vx_grad_opts_default(C.byref(o))
+    o.mode, o.beta, o.cg_rtol, o.cg_max_iter, o.cost = mode, beta, cg_rtol, cg_max_iter, cost
+    o.ep_f64 = ep_f64
+    if cost_data is not None:
+        o.cost_data = cost_data.data_ptr()
+    if inner is not None:
+        o.inner = min_opts(**inner)
+    st = capi.vx_equilibrium_grad_async(t.handle, _ptr(Xstar), C.byref(prm.struct), _ptr(dCdX),
+                                        C.byref(o), _ptr(g.get("lam")), _ptr(g.get("A0")),
+                                        _ptr(g.get("P0")), C.c_void_p(result.data_ptr()),
+                                        _stream())
+    capi.check(st, "vx_equilibrium_grad_async")
+    return prm
+
+
 def vx_minimize_many(tissues, Xs, params, **opts):
     """Relax several tissues in one launch (see vx.h).  Xs: list of device
     f64 [V_k, 2] tensors updated in place; params: one dict per tissue (or
@@ -264,7 +335,7 @@ class GradResult:
 
 def vx_equilibrium_grad(t: Tissue, Xstar, params, dCdX=None, mode=VX_ADJOINT_CG, beta=1e-3,
                         cg_rtol=1e-10, cg_max_iter=20000, cost=VX_COST_NONE, cost_data=None,
-                        inner=None):
+                        inner=None, ep_f64=0):
     """Gradient of the outer cost at the equilibrium X* with respect to
     (Lambda, A0, P0).  Returns (dict of device f64 tensors, GradResult)."""
     torch = _torch()
@@ -273,6 +344,7 @@ def vx_equilibrium_grad(t: Tissue, Xstar, params, dCdX=None, mode=VX_ADJOINT_CG,
     o = capi.vx_grad_opts()
     capi.vx_grad_opts_default(C.byref(o))
     o.mode, o.beta, o.cg_rtol, o.cg_max_iter, o.cost = mode, beta, cg_rtol, cg_max_iter, cost
+    o.ep_f64 = ep_f64
     cd = None
     if cost_data is not None:
         cd = _dev_f64(cost_data)
@@ -481,6 +553,17 @@ def vx_equilibrium_grad_batched(b: Batch, Xstar, params, dCdX, cg_rtol=1e-10, cg
         capi.check(st, "vx_equilibrium_grad_batched")
     return g, [GradResult(x.status, x.cg_iters, x.cg_rel_residual, x.cost, tuple(x.nudged_iters))
                for x in r]
+
+
+def vx_grid_barrier_selftest(ctas, absent_rank=-1, rounds=8, wait_s=0.25):
+    """Bounded-wait check of the GRID barrier (see vx.h).  Returns (status,
+    per-CTA statuses)."""
+    out = np.zeros(ctas, dtype=np.int32)
+    st = capi.vx_grid_barrier_selftest(ctas, absent_rank, rounds, wait_s, out.ctypes.data,
+                                       _stream())
+    if st not in (capi.VX_OK, capi.VX_ERR_TIMEOUT):
+        capi.check(st, "vx_grid_barrier_selftest")
+    return st, out
 
 
 def vx_batch_autotune(b: Batch, X, params, probe_iters=200, **opts):

@@ -48,7 +48,8 @@ class vx_min_opts(C.Structure):
                 ("max_iter", C.c_int32), ("gd_lr", C.c_double), ("dt0", C.c_double),
                 ("dt_max", C.c_double), ("n_min", C.c_int32), ("f_inc", C.c_double),
                 ("f_dec", C.c_double), ("alpha0", C.c_double), ("f_alpha", C.c_double),
-                ("l_min", C.c_double), ("path", C.c_int32), ("check_every", C.c_int32)]
+                ("l_min", C.c_double), ("path", C.c_int32), ("check_every", C.c_int32),
+                ("wrap", C.c_int32), ("edge_events", C.c_void_p)]
 
 
 class vx_min_result(C.Structure):
@@ -61,7 +62,7 @@ class vx_min_result(C.Structure):
 class vx_grad_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("beta", C.c_double), ("cg_rtol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("cost", C.c_int32), ("cost_data", C.c_void_p),
-                ("inner", vx_min_opts)]
+                ("inner", vx_min_opts), ("ep_f64", C.c_int32)]
 
 
 class vx_grad_result(C.Structure):
@@ -118,6 +119,13 @@ vx_energy_forces_noalloc = _sig("vx_energy_forces_noalloc", C.c_int, C.c_void_p,
                                 C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p,
                                 C.POINTER(vx_params), C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p)
+vx_minimize_async = _sig("vx_minimize_async", C.c_int, C.c_void_p, C.c_void_p,
+                         C.POINTER(vx_params), C.POINTER(vx_min_opts), C.c_void_p, C.c_void_p)
+vx_equilibrium_grad_async = _sig("vx_equilibrium_grad_async", C.c_int, C.c_void_p, C.c_void_p,
+                                 C.POINTER(vx_params), C.c_void_p, C.POINTER(vx_grad_opts),
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+vx_grid_barrier_selftest = _sig("vx_grid_barrier_selftest", C.c_int, C.c_int32, C.c_int32,
+                                C.c_int32, C.c_double, C.c_void_p, C.c_void_p)
 vx_batch_create = _sig("vx_batch_create", C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                        C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p))
 vx_batch_destroy = _sig("vx_batch_destroy", C.c_int, C.c_void_p)
@@ -144,7 +152,8 @@ EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx
             "vx_min_opts_default", "vx_minimize", "vx_minimize_many", "vx_grad_opts_default",
             "vx_equilibrium_grad",
             "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
-            "vx_batch_topology", "vx_energy_forces_noalloc",
+            "vx_batch_topology", "vx_energy_forces_noalloc", "vx_grid_barrier_selftest",
+            "vx_minimize_async", "vx_equilibrium_grad_async",
             "vx_minimize_batched", "vx_batch_autotune", "vx_equilibrium_grad_batched",
             "vx_batch_aniso_cost"]
 

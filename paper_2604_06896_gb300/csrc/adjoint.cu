@@ -1,8 +1,7 @@
-// Equilibrium gradients (Methods, "Gradient computation methods"):
-//   adjoint implicit differentiation through the persistent CG kernels, and
-//   equilibrium propagation through two nudged persistent minimisations
-//   followed by the difference of d_theta E; plus the Hessian-vector product
-//   entry point.
+// Kernels of the equilibrium gradients (Methods, "Gradient computation
+// methods"; the drivers are in grad.cu): the equilibrium-propagation
+// difference of d_theta E, the v2v cost, the anisotropy cost and its
+// gradient; plus the Hessian-vector product entry point.
 #include <cuda_runtime.h>
 
 #include "persistent.cuh"
@@ -11,12 +10,7 @@
 
 namespace vx {
 
-vx_status adjoint_solve(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
-                        int path, AdjOut* out, cudaStream_t s);
-bool resident_fits(vx_tissue_s* t, bool adjoint);
-bool cluster_fits(vx_tissue_s* t);
-
-static View<PolF64> topo_view(vx_tissue_s* t, const double* X) {
+View<PolF64> topo_view(vx_tissue_s* t, const double* X) {
   View<PolF64> v;
   v.X = (double2*)X;
   v.tgt = t->tgt;
@@ -195,145 +189,10 @@ vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double*
   return VX_OK;
 }
 
+// The solver region of the workspace (allocated by vx_tissue_create) holds
+// `doubles`; nothing is allocated here.
 bool ensure_work(vx_tissue_s* t, size_t doubles) {
-  if (t->work_doubles >= doubles) return true;
-  if (t->work) cudaFree(t->work);
-  t->work = nullptr;
-  t->work_doubles = 0;
-  if (cudaMalloc(&t->work, 8 * doubles) != cudaSuccess) return false;
-  t->work_doubles = doubles;
-  return true;
-}
-
-vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
-                           const double* dCdX, const vx_grad_opts* o, double* g_lambda, double* g_A0,
-                           double* g_P0, vx_grad_result* r, cudaStream_t s) {
-  if (o->cost == VX_COST_ANISO && o->mode != VX_ADJOINT_CG) {
-    set_error("equilibrium propagation with the anisotropy cost is not available in this build");
-    return VX_ERR_INVALID_ARG;
-  }
-  double* aniso_grad = nullptr;
-  double aniso_cost = 0.0;
-  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_ANISO) {
-    // C and grad_X C of the shape-tensor anisotropy, in FP64, into a buffer
-    // of its own (the adjoint workspace may be reallocated by the solve).
-    const int nb = (t->n + 255) / 256;
-    const size_t need = 2 * (size_t)t->V + 2 * (size_t)t->n + (size_t)t->n + 3 * (size_t)nb + 8;
-    double* buf = nullptr;
-    if (cudaMalloc(&buf, 8 * need) != cudaSuccess) {
-      set_error("out of device memory for the anisotropy cost");
-      return VX_ERR_OOM;
-    }
-    double* gradX = buf;
-    double2* cent = (double2*)(buf + 2 * (size_t)t->V);
-    int* kk = (int*)(buf + 2 * (size_t)t->V + 2 * (size_t)t->n);
-    double* part = buf + 2 * (size_t)t->V + 3 * (size_t)t->n;
-    double* g = part + 3 * (size_t)nb;
-    View<PolF64> vs = topo_view(t, Xstar);
-    vs.ccor = nullptr;
-    k_aniso_cells<<<nb, 256, 0, s>>>(vs, cent, kk, part);
-    k_aniso_final<<<1, 32, 0, s>>>(part, nb, t->n, o->cost_data, g);
-    k_aniso_grad<<<(t->V + 255) / 256, 256, 0, s>>>(vs, cent, kk, g, (double2*)gradX);
-    if (cudaMemcpyAsync(&aniso_cost, g, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      cudaFree(buf);
-      set_error(std::string("anisotropy cost: ") + cudaGetErrorString(cudaGetLastError()));
-      return VX_ERR_CUDA;
-    }
-    aniso_grad = buf;
-  }
-  if (o->mode == VX_ADJOINT_CG) {
-    AdjParams ap = {};
-    ap.dCdX = aniso_grad ? aniso_grad : dCdX;
-    ap.cost = o->cost;
-    ap.cost_data = o->cost_data;
-    ap.rtol = o->cg_rtol;
-    ap.max_iter = o->cg_max_iter;
-    ap.g_lam = g_lambda;
-    ap.g_A0 = g_A0;
-    ap.g_P0 = g_P0;
-    AdjOut out = {};
-    // the plain path runs the same CG as one launch per sub-step
-    const vx_status st = o->inner.path == VX_PATH_PLAIN
-                             ? adjoint_plain(t, Xstar, prm, ap, o->inner.check_every, &out, s)
-                             : adjoint_solve(t, Xstar, prm, ap, o->inner.path, &out, s);
-    if (aniso_grad) cudaFree(aniso_grad);
-    if (st != VX_OK) return st;
-    r->status = out.status;
-    r->cg_iters = out.iters;
-    r->cg_rel_residual = out.rel_residual;
-    r->cost = dCdX ? 0.0 : (aniso_grad ? aniso_cost : out.cost);
-    r->nudged_iters[0] = r->nudged_iters[1] = 0;
-    if (out.status == VX_ERR_INDEFINITE) {
-      set_error("CG met a direction of non-positive curvature (the Hessian is not positive definite)");
-      return VX_ERR_INDEFINITE;
-    }
-    return VX_OK;
-  }
-  // Equilibrium propagation.
-  if (!resident_fits(t, false) && !cluster_fits(t)) {
-    set_error("equilibrium propagation needs the resident or cluster minimiser");
-    return VX_ERR_INVALID_ARG;
-  }
-  const size_t V2 = 2 * (size_t)t->V;
-  if (!ensure_work(t, 2 * V2 + 8)) {
-    set_error("out of device memory for the equilibrium-propagation workspace");
-    return VX_ERR_OOM;
-  }
-  double* Xp = t->work;
-  double* Xm = t->work + V2;
-  double* cst = t->work + 2 * V2;
-  MinParams mp = {};
-  const vx_min_opts& in = o->inner;
-  mp.method = in.method;
-  mp.tol = in.tol;
-  mp.patience = in.patience;
-  mp.max_iter = in.max_iter;
-  mp.gd_lr = in.gd_lr;
-  mp.dt0 = in.dt0;
-  mp.dt_max = in.dt_max;
-  mp.n_min = in.n_min;
-  mp.f_inc = in.f_inc;
-  mp.f_dec = in.f_dec;
-  mp.alpha0 = in.alpha0;
-  mp.f_alpha = in.f_alpha;
-  mp.l_min = 0.0;  // fixed topology in the nudged phases
-  mp.cost = 1;
-  mp.cost_data = o->cost_data;
-  const bool centered = o->mode == VX_EP_CENTERED;
-  const int path = in.path == VX_PATH_PLAIN ? VX_PATH_AUTO : in.path;
-  if (cudaMemcpyAsync(Xp, Xstar, 8 * V2, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(Xm, Xstar, 8 * V2, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-    set_error("vx_equilibrium_grad: copy failed");
-    return VX_ERR_CUDA;
-  }
-  MinOut op = {}, om = {};
-  int used = 0;
-  mp.nudge_s = centered ? 0.5 * o->beta : o->beta;
-  vx_status st = minimize(t, Xp, prm, mp, path, in.check_every, &op, &used, s);
-  if (st != VX_OK) return st;
-  if (centered) {
-    mp.nudge_s = -0.5 * o->beta;
-    st = minimize(t, Xm, prm, mp, path, in.check_every, &om, &used, s);
-    if (st != VX_OK) return st;
-  }
-  View<PolF64> vp = topo_view(t, Xp), vm = topo_view(t, Xm), vs = topo_view(t, Xstar);
-  const int nb = (t->E + 255) / 256;
-  k_ep_grad<<<nb, 256, 0, s>>>(vp, vm, prm, o->beta, g_lambda, g_A0, g_P0);
-  k_v2v_cost<<<1, 256, 0, s>>>(vs, o->cost_data, cst);
-  double c = 0;
-  if (cudaMemcpyAsync(&c, cst, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    set_error(std::string("equilibrium propagation: ") + cudaGetErrorString(cudaGetLastError()));
-    return VX_ERR_CUDA;
-  }
-  r->status = (op.status == VX_OK && (!centered || om.status == VX_OK)) ? VX_OK : VX_NOT_CONVERGED;
-  r->cg_iters = 0;
-  r->cg_rel_residual = 0;
-  r->cost = c;
-  r->nudged_iters[0] = op.iters;
-  r->nudged_iters[1] = centered ? om.iters : 0;
-  return VX_OK;
+  return t->work && doubles <= work_solver_doubles(t->n, t->V);
 }
 
 // ------------------------------------------------------ Hessian x vector

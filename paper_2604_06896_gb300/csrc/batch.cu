@@ -53,9 +53,15 @@ struct vx_batch_s {
   cudaGraphExec_t gexec;
   std::vector<unsigned char> gkey;
   // batched adjoint: per-cell 4-vectors, CG vectors x, r, p, z, inverse
-  // diagonal blocks (allocated at the first gradient call)
+  // diagonal blocks (sized by adj_ws_bytes)
   void* adj_ws;
   vx::AdjOut* d_adj_out;
+  // anisotropy cost: centroids double2 [n_tot], corner counts int [n_tot],
+  // costs [count]; autotuner's copy of the positions [V_tot][2]
+  double* aniso_ws;
+  double* Xtune;
+  // image shifts of the exit-time wrap [V_tot]
+  int2* wrapk;
 };
 
 namespace vx {
@@ -277,6 +283,110 @@ static cudaError_t launch_adj_batch(const BatchAdjArgs& a, int count, cudaStream
   return cudaGetLastError();
 }
 
+// The anisotropy cost of every tissue and its gradient, one CTA per tissue
+// at a time: the cells' centroids and shape tensors (FP64), Q = mean S by a
+// fixed-order block reduction, then grad_X C per vertex (the cost's
+// definition is in persistent.cuh).
+__global__ void k_aniso_batch(const BatchDesc* desc, int count, const uint32_t* tgt,
+                              const int32_t* nxt, const int32_t* face, const int32_t* vout,
+                              const int32_t* ffirst, const double* X, const double* qt,
+                              double2* cent, int* kk, double2* grad, double* C) {
+  __shared__ double red[3][32];
+  __shared__ double G[3];
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const BatchDesc d = desc[k];
+    View<PolF64> v;
+    v.X = (double2*)(X + 2 * (size_t)d.vbase);
+    v.tgt = (uint32_t*)tgt + d.hbase;
+    v.nxt = (int32_t*)nxt + d.hbase;
+    v.face = (int32_t*)face + d.hbase;
+    v.vout = (int32_t*)vout + 3 * (size_t)d.vbase;
+    v.ffirst = (int32_t*)ffirst + d.cbase;
+    v.n = d.n;
+    v.V = d.V;
+    v.E = d.E;
+    v.box = PolF64::make_box(d.Lx, d.Ly);
+    v.Lx = d.Lx;
+    v.Ly = d.Ly;
+    v.vnb = nullptr;
+    v.vfc = nullptr;
+    v.ccnt = nullptr;
+    v.ccor = nullptr;
+    v.cedge = nullptr;
+    double2* ck = cent + d.cbase;
+    int* kc = kk + d.cbase;
+    double Q[3] = {0, 0, 0};
+    for (int c = threadIdx.x; c < d.n; c += blockDim.x) {
+      double sxx, syy, sxy;
+      cell_shape(v, c, ck, kc, sxx, syy, sxy);
+      Q[0] += sxx;
+      Q[1] += syy;
+      Q[2] += sxy;
+    }
+    for (int q = 0; q < 3; ++q) {
+      const double x = warp_sum(Q[q]);
+      if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double Qm[3] = {0, 0, 0};
+      for (int q = 0; q < 3; ++q) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Qm[q] += red[q][w];
+        Qm[q] /= d.n;
+      }
+      double g[3];
+      aniso_dC_dQ(Qm, qt, g);
+      const double T = Qm[0] + Qm[1];
+      const double q1 = (Qm[0] - Qm[1]) / T - qt[0], q2 = 2.0 * Qm[2] / T - qt[1];
+      C[k] = q1 * q1 + q2 * q2;
+      G[0] = g[0];
+      G[1] = g[1];
+      G[2] = g[2];
+    }
+    __syncthreads();
+    const double Gl[3] = {G[0], G[1], G[2]};
+    for (int i = threadIdx.x; i < d.V; i += blockDim.x) {
+      double gx, gy;
+      aniso_grad_vertex(v, i, ck, kc, Gl, gx, gy);
+      grad[d.vbase + i] = make_double2(gx, gy);
+    }
+    __syncthreads();
+  }
+}
+
+// Exit-time wrap of every tissue (Methods, "Periodic mode"): positions back
+// into the tissue's box, offsets fixed so that the unwrapped edge vectors
+// keep their values.  One CTA per tissue at a time; an offset that would
+// leave {-1, 0, 1} is left unchanged and flagged in the tissue's result.
+__global__ void k_wrap_batch(const BatchDesc* desc, int count, double* X, uint32_t* tgt, int2* kv,
+                             MinOut* out) {
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const BatchDesc d = desc[k];
+    double* Xk = X + 2 * (size_t)d.vbase;
+    int2* kk = kv + d.vbase;
+    uint32_t* tk = tgt + d.hbase;
+    for (int i = threadIdx.x; i < d.V; i += blockDim.x) {
+      int kx, ky;
+      Xk[2 * i] = wrap_coord(Xk[2 * i], d.Lx, kx);
+      Xk[2 * i + 1] = wrap_coord(Xk[2 * i + 1], d.Ly, ky);
+      kk[i] = make_int2(kx, ky);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < d.E; e += blockDim.x) {
+      const uint32_t t0 = tk[2 * e], t1 = tk[2 * e + 1];
+      const int a = tgt_v(t1), b = tgt_v(t0);
+      const int ox = tgt_ox(t0) + kk[b].x - kk[a].x, oy = tgt_oy(t0) + kk[b].y - kk[a].y;
+      if (ox < -1 || ox > 1 || oy < -1 || oy > 1) {
+        out[k].wrap_err = VX_ERR_TOPOLOGY;
+        continue;
+      }
+      tk[2 * e] = pack_tgt(b, ox, oy);
+      tk[2 * e + 1] = pack_tgt(a, -ox, -oy);
+    }
+    __syncthreads();
+  }
+}
+
 template <class P, int T>
 static cudaError_t launch_batch_t(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
   // the shared-memory attribute was set by occupancy() before any capture
@@ -320,6 +430,26 @@ vx_status fail(vx_status s, const std::string& m) {
 
 bool same_key(const std::vector<unsigned char>& a, const unsigned char* b, size_t n) {
   return a.size() == n && std::memcmp(a.data(), b, n) == 0;
+}
+
+size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace of the batched adjoint: per-cell 4-vectors, then the CG vectors
+// x, r, p, z [V][2] and the inverse diagonal blocks [V][4].
+struct AdjLayout {
+  size_t o_x, vec, o_pre, bytes;
+};
+AdjLayout adj_layout(int dtype, size_t n_tot, size_t V_tot) {
+  const size_t rs = dtype == VX_F64 ? 8 : 4;  // bytes of one real
+  AdjLayout l;
+  l.o_x = r256(4 * rs * n_tot);
+  l.vec = r256(2 * rs * V_tot);
+  l.o_pre = l.o_x + 4 * l.vec;
+  l.bytes = l.o_pre + r256(4 * rs * V_tot);
+  return l;
+}
+size_t adj_ws_bytes(int dtype, size_t n_tot, size_t V_tot) {
+  return adj_layout(dtype, n_tot, V_tot).bytes;
 }
 
 }  // namespace
@@ -428,6 +558,11 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   A((void**)&b->shortbits, 4 * (size_t)sb);
   A((void**)&b->touched, 4 * (size_t)tb);
   A((void**)&b->d_out, sizeof(vx::MinOut) * count);
+  A((void**)&b->wrapk, sizeof(int2) * (size_t)vb);
+  A(&b->adj_ws, adj_ws_bytes(b->dtype, nb, vb));
+  A((void**)&b->d_adj_out, sizeof(vx::AdjOut) * count);
+  A((void**)&b->aniso_ws, 8 * (3 * (size_t)nb + (size_t)count + 8));
+  A((void**)&b->Xtune, 16 * (size_t)vb);
   if (e != cudaSuccess) {
     vx_batch_destroy(b);
     return fail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA,
@@ -459,7 +594,7 @@ vx_status vx_batch_destroy(vx_batch b) {
   void* ptrs[] = {b->d_desc, b->d_order, b->d_counter, b->tgt,  b->nxt,   b->face,  b->vout,
                   b->ffirst, b->tgt0,    b->nxt0,      b->face0, b->vout0, b->ffirst0, b->Xw,
                   b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out,
-                  b->adj_ws, b->d_adj_out};
+                  b->adj_ws, b->d_adj_out, b->wrapk, b->aniso_ws, b->Xtune};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -586,8 +721,12 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4, s);
     if (e != cudaSuccess) return e;
-    return f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
-               : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
+    e = f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
+            : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
+    if (e != cudaSuccess || !mp.wrap) return e;
+    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(b->d_desc, b->count, X, b->tgt,
+                                                              b->wrapk, b->d_out);
+    return cudaGetLastError();
   };
   cudaError_t e;
   if (!use_graph) {
@@ -656,6 +795,8 @@ vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p, c
   mp.alpha0 = o->alpha0;
   mp.f_alpha = o->f_alpha;
   mp.l_min = o->l_min;
+  mp.wrap = o->wrap ? 1 : 0;
+  mp.edge_events = nullptr;
   const vx_status st = run_batch(b, X, p, mp, b->threads, b->smem_bytes, s, true);
   if (st != VX_OK) return st;
   std::vector<vx::MinOut> out(b->count);
@@ -674,6 +815,7 @@ vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p, c
     r[k].energy = out[k].energy;
     r[k].path_used = VX_PATH_RESIDENT;
     r[k].force_evals = out[k].force_evals;
+    if (out[k].wrap_err) r[k].status = VX_ERR_TOPOLOGY;
   }
   return VX_OK;
 }
@@ -686,9 +828,9 @@ vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p, con
   set_tissue_params(b, p);
   cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
                   cudaMemcpyHostToDevice, s);
-  // Scratch copy of X: the probes must not move the caller's positions.
-  double* Xs = nullptr;
-  if (cudaMalloc(&Xs, 16 * (size_t)b->V_tot) != cudaSuccess) return fail(VX_ERR_OOM, "autotune scratch");
+  // Scratch copy of X (allocated with the batch): the probes must not move
+  // the caller's positions.
+  double* Xs = b->Xtune;
   vx::MinParams mp = {};
   mp.method = o->method;
   mp.tol = o->tol;
@@ -732,7 +874,6 @@ vx_status vx_batch_autotune(vx_batch b, double* X, const vx_batch_params* p, con
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(Xs);
   vx_batch_restore(b, stream);
   b->threads = bt;
   b->smem_bytes = bs;
@@ -753,20 +894,8 @@ vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_
   if (cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(VX_ERR_CUDA, "descriptor upload");
-  const size_t rs = b->dtype == VX_F64 ? 8 : 4;  // bytes of one real
-  auto r256 = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t o_x = r256(4 * rs * (size_t)b->n_tot);
-  const size_t vec = r256(2 * rs * (size_t)b->V_tot);
-  const size_t o_pre = o_x + 4 * vec;
-  const size_t bytes = o_pre + r256(4 * rs * (size_t)b->V_tot);
-  if (!b->adj_ws && cudaMalloc(&b->adj_ws, bytes) != cudaSuccess) {
-    b->adj_ws = nullptr;
-    return fail(VX_ERR_OOM, "out of device memory for the batched adjoint");
-  }
-  if (!b->d_adj_out && cudaMalloc((void**)&b->d_adj_out, sizeof(vx::AdjOut) * b->count) != cudaSuccess) {
-    b->d_adj_out = nullptr;
-    return fail(VX_ERR_OOM, "out of device memory for the batched adjoint");
-  }
+  const AdjLayout L = adj_layout(b->dtype, b->n_tot, b->V_tot);
+  const size_t o_x = L.o_x, vec = L.vec, o_pre = L.o_pre;
   unsigned char* w = (unsigned char*)b->adj_ws;
   vx::BatchAdjArgs a = {};
   a.desc = b->d_desc;
@@ -828,36 +957,20 @@ vx_status vx_batch_aniso_cost(vx_batch b, const double* X, const double* q_targe
                               double* dCdX, void* stream) {
   if (!b || !X || !q_target || !C || !dCdX) return fail(VX_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
-  int nmax = 0;
-  for (const BatchDesc& d : b->desc) nmax = std::max(nmax, d.n);
-  double* scratch = nullptr;
-  if (cudaMalloc(&scratch, 8 * vx::aniso_scratch_doubles(nmax)) != cudaSuccess)
-    return fail(VX_ERR_OOM, "out of device memory for the anisotropy cost");
-  vx_status st = VX_OK;
-  for (int k = 0; k < b->count && st == VX_OK; ++k) {
-    const BatchDesc& d = b->desc[k];
-    vx::View<vx::PolF64> v;
-    v.X = (double2*)(X + 2 * (size_t)d.vbase);
-    v.tgt = b->tgt + d.hbase;
-    v.nxt = b->nxt + d.hbase;
-    v.face = b->face + d.hbase;
-    v.vout = b->vout + 3 * (size_t)d.vbase;
-    v.ffirst = b->ffirst + d.cbase;
-    v.n = d.n;
-    v.V = d.V;
-    v.E = d.E;
-    v.box = vx::PolF64::make_box(d.Lx, d.Ly);
-    v.Lx = d.Lx;
-    v.Ly = d.Ly;
-    v.vnb = nullptr;
-    v.vfc = nullptr;
-    v.ccnt = nullptr;
-    v.ccor = nullptr;
-    v.cedge = nullptr;
-    st = vx::aniso_cost_view(v, q_target, dCdX + 2 * (size_t)d.vbase, scratch, &C[k], s);
-  }
-  cudaFree(scratch);
-  return st;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double2* cent = (double2*)b->aniso_ws;
+  int* kk = (int*)(b->aniso_ws + 2 * (size_t)b->n_tot);
+  double* Cd = b->aniso_ws + 3 * (size_t)b->n_tot;
+  vx::k_aniso_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(
+      b->d_desc, b->count, b->tgt, b->nxt, b->face, b->vout, b->ffirst, X, q_target, cent, kk,
+      (double2*)dCdX, Cd);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(C, Cd, 8 * (size_t)b->count, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? VX_OK
+                          : fail(VX_ERR_CUDA, std::string("vx_batch_aniso_cost: ") + cudaGetErrorString(e));
 }
 
 }  // extern "C"

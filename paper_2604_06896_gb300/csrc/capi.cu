@@ -251,8 +251,10 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   if (e == cudaSuccess) e = cudaMalloc(&t->ffirst0, bytes(4 * (size_t)n));
   if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(vx::FireCtrl));
   if (e == cudaSuccess) e = cudaMalloc(&t->dout, sizeof(vx::MinOut));
+  if (e == cudaSuccess) e = cudaMalloc(&t->wrapk, bytes(sizeof(int2) * (size_t)V));
   t->work = nullptr;
-  t->work_doubles = 0;
+  t->work_doubles = vx::work_total_doubles(n, V);
+  if (e == cudaSuccess) e = cudaMalloc(&t->work, 8 * t->work_doubles);
   if (e != cudaSuccess) {
     vx_tissue_destroy(t);
     set_error(std::string("vx_tissue_create: ") + cudaGetErrorString(e));
@@ -283,7 +285,7 @@ vx_status vx_tissue_destroy(vx_tissue t) {
                   t->vel,  t->F,     t->cellc,     t->shortbits, t->touched, t->partE,
                   t->partF, t->ctrl, t->dout,      t->work,    t->tgt0,   t->nxt0,
                   t->face0, t->vout0, t->ffirst0, t->vnb,   t->vfc,    t->ccnt,
-                  t->ccor,  t->cedge};
+                  t->ccor,  t->cedge, t->wrapk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -385,6 +387,8 @@ void vx_min_opts_default(vx_min_opts* o) {
   o->l_min = 0.0;
   o->path = VX_PATH_AUTO;
   o->check_every = 50;
+  o->wrap = 1;
+  o->edge_events = nullptr;
 }
 
 static bool min_opts_ok(const vx_min_opts* o, std::string* m) {
@@ -418,6 +422,8 @@ static vx::MinParams to_min_params(const vx_min_opts* o) {
   mp.alpha0 = o->alpha0;
   mp.f_alpha = o->f_alpha;
   mp.l_min = o->l_min;
+  mp.wrap = o->wrap ? 1 : 0;
+  mp.edge_events = o->edge_events;
   return mp;
 }
 
@@ -441,8 +447,9 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
   r->energy = out.energy;
   r->path_used = used;
   r->force_evals = out.force_evals;
-  const vx_status st = (vx_status)out.status;
-  return st == VX_ERR_NONFINITE || st == VX_ERR_TIMEOUT ? st : VX_OK;
+  if (out.wrap_err) r->status = VX_ERR_TOPOLOGY;
+  const vx_status st = (vx_status)r->status;
+  return st == VX_ERR_NONFINITE || st == VX_ERR_TIMEOUT || st == VX_ERR_TOPOLOGY ? st : VX_OK;
 }
 
 vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
@@ -476,8 +483,10 @@ vx_status vx_minimize_many(vx_tissue* tissues, int32_t count, double* const* X,
     r[k].energy = out[k].energy;
     r[k].path_used = paths[k];
     r[k].force_evals = out[k].force_evals;
-    if (out[k].status == VX_ERR_NONFINITE || out[k].status == VX_ERR_TIMEOUT)
-      worst = (vx_status)out[k].status;
+    if (out[k].wrap_err) r[k].status = VX_ERR_TOPOLOGY;
+    if (r[k].status == VX_ERR_NONFINITE || r[k].status == VX_ERR_TIMEOUT ||
+        r[k].status == VX_ERR_TOPOLOGY)
+      worst = (vx_status)r[k].status;
   }
   return worst;
 }
@@ -495,21 +504,91 @@ void vx_grad_opts_default(vx_grad_opts* o) {
   o->inner.tol = 1e-10;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The minimiser's device result block as the caller's vx_min_result (in
+// device or pinned host memory).
+__global__ void k_min_result(const vx::MinOut* o, int path, vx_min_result* r) {
+  if (threadIdx.x || blockIdx.x) return;
+  vx_min_result x;
+  x.status = o->wrap_err ? (int)VX_ERR_TOPOLOGY : o->status;
+  x.iters = o->iters;
+  x.n_t1 = o->n_t1;
+  x.n_stretch = o->n_stretch;
+  x.n_short_edges = o->n_short;
+  x.n_inverted = o->n_inverted;
+  x.fmax = o->fmax;
+  x.energy = o->energy;
+  x.path_used = path;
+  x.force_evals = o->force_evals;
+  *r = x;
+}
+
+std::string grad_opts_error(const double* dCdX, const vx_grad_opts* o) {
+  std::string m;
+  if (o->mode != VX_ADJOINT_CG && o->mode != VX_EP_CENTERED && o->mode != VX_EP_FORWARD)
+    return "unknown gradient mode";
+  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_NONE)
+    return "adjoint needs dCdX or a built-in cost";
+  if (o->mode != VX_ADJOINT_CG && o->cost == VX_COST_NONE)
+    return "equilibrium propagation needs a built-in cost";
+  if (o->cost != VX_COST_NONE && o->cost != VX_COST_V2V && o->cost != VX_COST_ANISO)
+    return "unknown cost";
+  if (o->cost != VX_COST_NONE && !o->cost_data) return "cost_data is NULL";
+  if (o->mode != VX_ADJOINT_CG && !(o->beta > 0)) return "beta must be positive";
+  if (!min_opts_ok(&o->inner, &m)) return m;
+  return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+vx_status vx_minimize_async(vx_tissue t, double* X, const vx_params* p, const vx_min_opts* o,
+                            vx_min_result* r, void* stream) {
+  if (!t || !X || !r) return invalid("NULL tissue, X or result");
+  std::string m;
+  if (!params_ok(p, &m) || !min_opts_ok(o, &m)) return invalid(m);
+  if (o->path == VX_PATH_PLAIN || o->path == VX_PATH_GRID)
+    return invalid("vx_minimize_async runs the resident or cluster path only");
+  cudaStream_t s = as_stream(stream);
+  int used = 0;
+  const vx_status st = vx::minimize_launch(t, X, to_params(p), to_min_params(o), o->path, t->dout,
+                                           &used, s);
+  if (st != VX_OK) return st;
+  k_min_result<<<1, 1, 0, s>>>(t->dout, used, r);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("vx_minimize_async: ") + cudaGetErrorString(e));
+    return VX_ERR_CUDA;
+  }
+  return VX_OK;
+}
+
+vx_status vx_equilibrium_grad_async(vx_tissue t, const double* Xstar, const vx_params* p,
+                                    const double* dCdX, const vx_grad_opts* o, double* g_lambda,
+                                    double* g_A0, double* g_P0, vx_grad_result* r, void* stream) {
+  if (!t || !Xstar || !o || !r) return invalid("NULL tissue, X*, opts or result");
+  std::string m;
+  if (!params_ok(p, &m)) return invalid(m);
+  m = grad_opts_error(dCdX, o);
+  if (!m.empty()) return invalid(m);
+  if (o->inner.path == VX_PATH_PLAIN || o->inner.path == VX_PATH_GRID)
+    return invalid("vx_equilibrium_grad_async runs the persistent paths only");
+  return vx::equilibrium_grad_impl(t, Xstar, to_params(p), dCdX, o, g_lambda, g_A0, g_P0, nullptr, r,
+                                   as_stream(stream));
+}
+
 vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params* p,
                               const double* dCdX, const vx_grad_opts* o, double* g_lambda,
                               double* g_A0, double* g_P0, vx_grad_result* r, void* stream) {
   if (!t || !Xstar || !o || !r) return invalid("NULL tissue, X*, opts or result");
   std::string m;
   if (!params_ok(p, &m)) return invalid(m);
-  if (o->mode != VX_ADJOINT_CG && o->mode != VX_EP_CENTERED && o->mode != VX_EP_FORWARD)
-    return invalid("unknown gradient mode");
-  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_NONE)
-    return invalid("adjoint needs dCdX or a built-in cost");
-  if (o->mode != VX_ADJOINT_CG && o->cost == VX_COST_NONE)
-    return invalid("equilibrium propagation needs a built-in cost");
-  if (o->cost != VX_COST_NONE && !o->cost_data) return invalid("cost_data is NULL");
-  if (o->mode != VX_ADJOINT_CG && !(o->beta > 0)) return invalid("beta must be positive");
-  if (!min_opts_ok(&o->inner, &m)) return invalid(m);
+  m = grad_opts_error(dCdX, o);
+  if (!m.empty()) return invalid(m);
   return vx::equilibrium_grad(t, Xstar, to_params(p), dCdX, o, g_lambda, g_A0, g_P0, r,
                               as_stream(stream));
 }

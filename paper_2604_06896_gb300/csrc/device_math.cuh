@@ -458,180 +458,28 @@ struct T1Stats {
 
 constexpr double kT1Stretch = 1.5;  // both candidates: length 1.5 l_min
 
-// The serial T1 pass (Methods, "T1 transitions"): edges flagged in
-// `shortbits` are taken in increasing id, each re-checked against the current
-// positions; for an edge shorter than lmin the stretch and the T1 candidates
-// (both of length 1.5 lmin about the old midpoint) are compared by energy and
-// the lower one kept.  A T1 is not a candidate when a cell losing the edge is
-// a triangle, when the four cells are not distinct, or when an offset would
-// leave {-1, 0, 1}.  Edges with a larger id that a change makes short are
-// flagged and handled in the same pass.  Vertices of changed edges are
-// flagged in `touched` (their velocities are reset by the caller).  Clears
-// `shortbits`.  Cells whose geometry changed are appended to `dirty` (up to
-// `dirty_cap`; `*n_dirty` may exceed it).
-template <class P>
-__device__ __noinline__ void t1_pass(View<P> v, const ParamsD& prm, double lmin, uint32_t* shortbits,
-                        uint32_t* touched, T1Stats* st, int* dirty, int dirty_cap,
-                        int* n_dirty) {
-  using Pos = typename P::Pos;
-  const int nwords = (v.E + 31) >> 5;
-  const double lnew = kT1Stretch * lmin;
-  for (int w = 0; w < nwords; ++w) {
-    while (shortbits[w]) {
-      const uint32_t bits = shortbits[w];
-      const int bit = __ffs(bits) - 1;
-      shortbits[w] = bits & (bits - 1);
-      const int e = (w << 5) + bit;
-      const int h = 2 * e, hq = h ^ 1;
-      if (edge_len_d(v, h) >= lmin) continue;
-      const int a = src_of(v, h), b = tgt_v(v.tgt[h]);
-      touched[a >> 5] |= 1u << (a & 31);
-      touched[b >> 5] |= 1u << (b & 31);
-      const int C1 = v.face[h], C2 = v.face[hq];
-      const int hp1 = prev_of(v, h), hn1 = v.nxt[h];
-      const int hp2 = prev_of(v, hq), hn2 = v.nxt[hq];
-      const int ta_p = hp1 ^ 1, tb_y = hn1 ^ 1, tb_z = hp2 ^ 1, tx_a = hn2 ^ 1;
-      const int C3 = v.face[ta_p], C4 = v.face[tb_z];
-      const int cells[4] = {C1, C2, C3, C4};
-      const int hes[5] = {h, hp1, hn1, hp2, hn2};
-      // Images of the neighbours in a's frame (stored X = U - k L).
-      const uint32_t tg_h = v.tgt[h];
-      const int kbx = tgt_ox(tg_h), kby = tgt_oy(tg_h);
-      const int kpx = tgt_ox(v.tgt[ta_p]), kpy = tgt_oy(v.tgt[ta_p]);
-      const int kxx = tgt_ox(v.tgt[hn2]), kxy = tgt_oy(v.tgt[hn2]);
-      const int kyx = kbx + tgt_ox(v.tgt[hn1]), kyy = kby + tgt_oy(v.tgt[hn1]);
-      const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
-      bool allow = face_size(v, h) > 3 && face_size(v, hq) > 3 &&
-                   (!v.ccor || (face_size(v, ta_p) < kMaxCorners &&
-                                face_size(v, tb_z) < kMaxCorners)) &&
-                   C1 != C2 && C1 != C3 &&
-                   C1 != C4 && C2 != C3 && C2 != C4 && C3 != C4 && kyx >= -1 && kyx <= 1 &&
-                   kyy >= -1 && kyy <= 1 && kzx >= -1 && kzx <= 1 && kzy >= -1 && kzy <= 1;
-      // Geometry in a's frame.
-      double dx, dy;
-      edge_vec_d(v, h, dx, dy);
-      const double ell = sqrt(dx * dx + dy * dy);
-      const double ux = dx / ell, uy = dy / ell;
-      const double2 Xa = P::to_d(v.X[a]);
-      const double mx = Xa.x + 0.5 * dx, my = Xa.y + 0.5 * dy;
-      const Pos Xa0 = v.X[a], Xb0 = v.X[b];
-      // Candidate 1: stretch (b stays in its own frame).
-      const Pos Xas = P::from_d(mx - 0.5 * lnew * ux, my - 0.5 * lnew * uy);
-      const Pos Xbs = P::from_d(mx + 0.5 * lnew * ux - kbx * v.Lx, my + 0.5 * lnew * uy - kby * v.Ly);
-      v.X[a] = Xas;
-      v.X[b] = Xbs;
-      double Es = 0.0;
-      for (int k = 0; k < 4; ++k) Es += cell_energy_d(v, cells[k], prm);
-      for (int k = 0; k < 5; ++k) Es += prm.la(hes[k] >> 1) * edge_len_d(v, hes[k]);
-      bool take_t1 = false;
-      if (allow) {
-        // Save what a T1 rewrites.
-        const int sv_nxt_i[6] = {hp1, hp2, tx_a, hq, tb_y, h};
-        int sv_nxt[6];
-        for (int k = 0; k < 6; ++k) sv_nxt[k] = v.nxt[sv_nxt_i[k]];
-        const int sv_tgt_i[10] = {ta_p, hp1, hn1, tb_y, hn2, tx_a, tb_z, hp2, h, hq};
-        uint32_t sv_tgt[10];
-        for (int k = 0; k < 10; ++k) sv_tgt[k] = v.tgt[sv_tgt_i[k]];
-        const int sv_face[2] = {v.face[h], v.face[hq]};
-        int sv_vout[6];
-        for (int k = 0; k < 3; ++k) {
-          sv_vout[k] = v.vout[k * v.V + a];
-          sv_vout[3 + k] = v.vout[k * v.V + b];
-        }
-        const int sv_ff[2] = {v.ffirst[C1], v.ffirst[C2]};
-        const int p = tgt_v(v.tgt[ta_p]), y = tgt_v(v.tgt[hn1]);
-        const int x = tgt_v(v.tgt[hn2]), z = tgt_v(v.tgt[tb_z]);
-        // Candidate 2: T1.  a joins p and y on C1's side, b joins x and z.
-        const double px = -uy, py = ux;  // into C1
-        v.X[a] = P::from_d(mx + 0.5 * lnew * px, my + 0.5 * lnew * py);
-        v.X[b] = P::from_d(mx - 0.5 * lnew * px, my - 0.5 * lnew * py);
-        v.nxt[hp1] = hn1;
-        v.nxt[hp2] = hn2;
-        v.nxt[tx_a] = hq;
-        v.nxt[hq] = ta_p;
-        v.nxt[tb_y] = h;
-        v.nxt[h] = tb_z;
-        v.face[hq] = C3;
-        v.face[h] = C4;
-        v.tgt[ta_p] = pack_tgt(p, kpx, kpy);
-        v.tgt[hp1] = pack_tgt(a, -kpx, -kpy);
-        v.tgt[hn1] = pack_tgt(y, kyx, kyy);
-        v.tgt[tb_y] = pack_tgt(a, -kyx, -kyy);
-        v.tgt[hn2] = pack_tgt(x, kxx, kxy);
-        v.tgt[tx_a] = pack_tgt(b, -kxx, -kxy);
-        v.tgt[tb_z] = pack_tgt(z, kzx, kzy);
-        v.tgt[hp2] = pack_tgt(b, -kzx, -kzy);
-        v.tgt[h] = pack_tgt(b, 0, 0);
-        v.tgt[hq] = pack_tgt(a, 0, 0);
-        v.vout[a] = h;
-        v.vout[v.V + a] = hn1;
-        v.vout[2 * v.V + a] = ta_p;
-        v.vout[b] = hq;
-        v.vout[v.V + b] = hn2;
-        v.vout[2 * v.V + b] = tb_z;
-        if (v.ffirst[C1] == h) v.ffirst[C1] = hn1;
-        if (v.ffirst[C2] == hq) v.ffirst[C2] = hn2;
-        double Et = 0.0;
-        for (int k = 0; k < 4; ++k) Et += cell_energy_d(v, cells[k], prm);
-        for (int k = 0; k < 5; ++k) Et += prm.la(hes[k] >> 1) * edge_len_d(v, hes[k]);
-        if (Et < Es) {
-          take_t1 = true;
-        } else {
-          for (int k = 0; k < 6; ++k) v.nxt[sv_nxt_i[k]] = sv_nxt[k];
-          for (int k = 0; k < 10; ++k) v.tgt[sv_tgt_i[k]] = sv_tgt[k];
-          v.face[h] = sv_face[0];
-          v.face[hq] = sv_face[1];
-          for (int k = 0; k < 3; ++k) {
-            v.vout[k * v.V + a] = sv_vout[k];
-            v.vout[k * v.V + b] = sv_vout[3 + k];
-          }
-          v.ffirst[C1] = sv_ff[0];
-          v.ffirst[C2] = sv_ff[1];
-        }
-      }
-      if (take_t1) {
-        st->n_t1++;
-        if (v.ccor) {
-          const int p = tgt_v(v.tgt[ta_p]), y = tgt_v(v.tgt[hn1]);
-          const int x = tgt_v(v.tgt[hn2]), z = tgt_v(v.tgt[tb_z]);
-          const int ws[6] = {a, b, p, x, y, z};
-          for (int k = 0; k < 6; ++k) rebuild_vertex(v, ws[k]);
-          for (int k = 0; k < 4; ++k) rebuild_cell(v, cells[k]);
-        }
-      } else {
-        v.X[a] = Xas;
-        v.X[b] = Xbs;
-        st->n_stretch++;
-      }
-      (void)Xa0;
-      (void)Xb0;
-      for (int k = 0; k < 4; ++k) {
-        if (*n_dirty < dirty_cap) dirty[*n_dirty] = cells[k];
-        ++*n_dirty;
-      }
-      // Edges at a or b with a larger id that are now short join this pass.
-      for (int s = 0; s < 2; ++s) {
-        const int vv = s ? b : a;
-        for (int k = 0; k < 3; ++k) {
-          const int hh = v.vout[k * v.V + vv];
-          const int f = hh >> 1;
-          if (f > e && edge_len_d(v, hh) < lmin) shortbits[f >> 5] |= 1u << (f & 31);
-        }
-      }
-    }
-  }
-}
-
-// Warp-cooperative form of t1_pass: the same decisions in the same order,
-// executed by the 32 lanes of one warp.  Lane 0 does the bookkeeping and the
-// writes; lanes 0..3 evaluate the four cells and lanes 4..8 the five edges of
-// a candidate in parallel (energies summed with a fixed shuffle tree); the
-// flat-table rebuild is spread over lanes as well.  Every lane must call it.
+// The T1 pass (Methods, "T1 transitions"), executed by the 32 lanes of one
+// warp: edges flagged in `shortbits` are taken in increasing id, each
+// re-checked against the current positions; for an edge shorter than lmin
+// the stretch and the T1 candidates (both of length 1.5 lmin about the old
+// midpoint) are compared by energy and the lower one kept.  A T1 is not a
+// candidate when a cell losing the edge is a triangle, when the four cells
+// are not distinct, when an offset would leave {-1, 0, 1} or when a cell
+// would outgrow the flat tables.  Edges with a larger id that a change makes
+// short are flagged and handled in the same pass.  Vertices of changed edges
+// are flagged in `touched` (their velocities are reset by the caller).
+// Clears `shortbits`.  Cells whose geometry changed are appended to `dirty`
+// (up to `dirty_cap`; `*n_dirty` may exceed it).  `events` (optional, [E][2])
+// counts the stretches and T1s of every edge.
+// Lane 0 does the bookkeeping and the writes; lanes 0..3 evaluate the four
+// cells and lanes 4..8 the five edges of a candidate in parallel (energies
+// summed with a fixed shuffle tree); the flat-table rebuild is spread over
+// lanes as well.  Every lane must call it.
 template <class P>
 __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double lmin,
                                           uint32_t* shortbits, uint32_t* touched, T1Stats* st,
                                           int* dirty = nullptr, int dirty_cap = 0,
-                                          int* n_dirty = nullptr) {
+                                          int* n_dirty = nullptr, int* events = nullptr) {
   using Pos = typename P::Pos;
   const int lane = threadIdx.x & 31;
   const int nwords = (v.E + 31) >> 5;
@@ -783,6 +631,7 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
         }
       }
       __syncwarp();
+      if (lane == 0 && events) events[2 * e + (take_t1 ? 1 : 0)] += 1;
       if (take_t1) {
         if (lane == 0) st->n_t1++;
         if (v.ccor) {
@@ -818,6 +667,29 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
   }
   }
   __syncwarp();
+}
+
+// ------------------------------------------------------------ wrap
+
+// One coordinate of the exit-time wrap (Methods, "Periodic mode"):
+// x' = x - k L in [0, L) with k = floor(x / L), corrected by one period when
+// rounding left x' outside [0, L); a result that rounds to L is taken as 0.
+// Explicitly rounded operations: no fused multiply-add changes a result.
+__device__ __forceinline__ double wrap_coord(double x, double L, int& k) {
+  const double q = floor(__ddiv_rn(x, L));
+  double w = __dsub_rn(x, __dmul_rn(q, L));
+  int kk = (int)q;
+  if (w >= L) {
+    w = __dsub_rn(w, L);
+    ++kk;
+  }
+  if (w < 0.0) {
+    w = __dadd_rn(w, L);
+    --kk;
+  }
+  if (w >= L) w = 0.0;
+  k = kk;
+  return w;
 }
 
 // ------------------------------------------------------------ reductions

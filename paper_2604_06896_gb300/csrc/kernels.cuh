@@ -20,7 +20,15 @@ struct MinParams {
   // Nudged phase of equilibrium propagation: force += -s Pi grad_X C.
   int cost;              // 0 none, 1 v2v, 2 anisotropy
   double nudge_s;
-  const double* cost_data;
+  const double* cost_data;  // X_target [V][2] (v2v) or q_target [2] (anisotropy)
+  // anisotropy nudging: per-cell centroids double2 [n] followed by corner
+  // counts int [n] (global memory, any residency)
+  double* aniso_ws;
+  // Exit-time wrap of positions and offsets (applied by the host launcher
+  // after the solve).
+  int wrap;
+  // Optional per-edge decision counters [E][2] (stretches, T1s).
+  int* edge_events;
 };
 
 // Control block of the global-memory minimiser (one per tissue).
@@ -37,7 +45,8 @@ struct FireCtrl {
 
 // Result block written by the minimisers (device side).
 struct MinOut {
-  int status, iters, n_t1, n_stretch, n_short, n_inverted, force_evals, pad;
+  int status, iters, n_t1, n_stretch, n_short, n_inverted, force_evals;
+  int wrap_err;  // set by the exit-time wrap when an offset would leave {-1, 0, 1}
   double fmax, energy;
 };
 

@@ -118,7 +118,8 @@ __global__ void k_sum_energy(const double* partE, int nb, double* E, MinOut* out
 
 template <class P>
 __global__ void k_t1(View<P> v, ParamsD prm, double lmin, uint32_t* shortbits, uint32_t* touched,
-                     R2T<typename P::R>* vel, R2T<typename P::R>* cellc, FireCtrl* ctrl) {
+                     R2T<typename P::R>* vel, R2T<typename P::R>* cellc, FireCtrl* ctrl,
+                     int* events) {
   using R = typename P::R;
   constexpr int CAP = 512;
   __shared__ int dirty[CAP];
@@ -128,7 +129,7 @@ __global__ void k_t1(View<P> v, ParamsD prm, double lmin, uint32_t* shortbits, u
   __syncthreads();
   if (threadIdx.x < 32) {
     T1Stats st = {0, 0, 0};
-    t1_pass_warp(v, prm, lmin, shortbits, touched, &st, dirty, CAP, &n_dirty);
+    t1_pass_warp(v, prm, lmin, shortbits, touched, &st, dirty, CAP, &n_dirty, events);
     if (threadIdx.x == 0) {
       ctrl->n_t1 += st.n_t1;
       ctrl->n_stretch += st.n_stretch;
@@ -401,7 +402,8 @@ static vx_status minimize_plain(vx_tissue_s* t, double* X, const ParamsD& prm, c
   for (int it = 0; it <= mp.max_iter; ++it) {
     k_cells<P><<<nbc, th, 0, s>>>(v, prm, cellc, t->shortbits, mp.l_min, t->ctrl, nullptr);
     if (mp.l_min > 0)
-      k_t1<P><<<1, 256, 0, s>>>(v, prm, mp.l_min, t->shortbits, t->touched, vel, cellc, t->ctrl);
+      k_t1<P><<<1, 256, 0, s>>>(v, prm, mp.l_min, t->shortbits, t->touched, vel, cellc, t->ctrl,
+                                mp.edge_events);
     k_vertices<P, R2T<R>><<<nbv, th, 0, s>>>(v, cellc, prm.lam, prm.lam_s, F, vel, t->ctrl,
                                              t->partF, mp);
     k_update<P><<<nbv, th, 0, s>>>(v, vel, F, t->ctrl, mp.method);
@@ -417,6 +419,7 @@ static vx_status minimize_plain(vx_tissue_s* t, double* X, const ParamsD& prm, c
   k_sum_energy<<<1, 32, 0, s>>>(t->partE, nbc, nullptr, t->dout);
   k_final_short<P><<<1, 32, 0, s>>>(v, mp.l_min, &t->dout->n_short);
   k_store_X<P><<<grid_for(t->V, th), th, 0, s>>>(v.X, X, t->V);
+  if (mp.wrap && wrap_tissue(t, X, &t->dout->wrap_err, s) != VX_OK) return VX_ERR_CUDA;
   MinOut o;
   cudaMemcpyAsync(&o, t->dout, sizeof(MinOut), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return VX_ERR_CUDA;
@@ -426,6 +429,7 @@ static vx_status minimize_plain(vx_tissue_s* t, double* X, const ParamsD& prm, c
   o.n_stretch = ch.n_stretch;
   o.fmax = sqrt(ch.fmax2);
   o.force_evals = ch.it + 1;
+  if (!mp.wrap) o.wrap_err = 0;
   *out_h = o;
   return VX_OK;
 }

@@ -40,36 +40,52 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
+// Status bits written by the kernels (see vx.h).
+constexpr int kBadValence = 1;
+constexpr int kBadIndex = 2;
+
 // Per cell: cA = 2 K_A (A - A0), cP = 2 K_P (P - P0) and its energy; one
 // partial energy per block (cell terms plus 1/2 Lambda l per half-edge).
+// Every table index is checked before it is used: an index out of range
+// sets kBadIndex and ends the cell's walk.
 __global__ void k_na_cells(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
                            int n, double Lx, double Ly, const double* X, ParamsD prm,
-                           double* scratch) {
+                           double* scratch, int* bad) {
   __shared__ double red[kNoAllocThreads / 32];
   double* cc = scratch;
   double* part = scratch + 2 * (size_t)kNoAllocMaxCells;
+  const int V = 2 * n, HE = 6 * n, E = 3 * n;
   double e = 0.0;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n) {
     const int h0 = face_he[c];
-    const int v0 = he[8 * h0 + 3];
-    const double x0 = X[2 * v0], y0 = X[2 * v0 + 1];
+    bool ok = h0 >= 0 && h0 < HE;
+    const int v0 = ok ? he[8 * h0 + 3] : 0;
+    ok = ok && v0 >= 0 && v0 < V;
     double qx = 0, qy = 0, A2 = 0, P = 0, el = 0;
-    int ox = 0, oy = 0, h = h0, guard = 0;
-    do {
-      const int32_t* r = he + 8 * h;
-      ox += r[6];
-      oy += r[7];
-      const int t = r[4];
-      const double nx = (X[2 * t] + ox * Lx) - x0, ny = (X[2 * t + 1] + oy * Ly) - y0;
-      A2 += qx * ny - nx * qy;
-      const double l = sqrt((nx - qx) * (nx - qx) + (ny - qy) * (ny - qy));
-      P += l;
-      el += 0.5 * prm.la(edge_id[h]) * l;
-      qx = nx;
-      qy = ny;
-      h = r[1];
-    } while (h != h0 && ++guard < 4096);
+    if (ok) {
+      const double x0 = X[2 * v0], y0 = X[2 * v0 + 1];
+      int ox = 0, oy = 0, h = h0, guard = 0;
+      do {
+        const int32_t* r = he + 8 * h;
+        const int t = r[4], eid = edge_id[h], hn = r[1];
+        if (t < 0 || t >= V || eid < 0 || eid >= E || hn < 0 || hn >= HE) {
+          ok = false;
+          break;
+        }
+        ox += r[6];
+        oy += r[7];
+        const double nx = (X[2 * t] + ox * Lx) - x0, ny = (X[2 * t + 1] + oy * Ly) - y0;
+        A2 += qx * ny - nx * qy;
+        const double l = sqrt((nx - qx) * (nx - qx) + (ny - qy) * (ny - qy));
+        P += l;
+        el += 0.5 * prm.la(eid) * l;
+        qx = nx;
+        qy = ny;
+        h = hn;
+      } while (h != h0 && ++guard < 4096);
+    }
+    if (!ok) atomicOr(bad, kBadIndex);
     const double dA = 0.5 * A2 - prm.a0(c), dP = P - prm.p0(c);
     cc[2 * c] = 2.0 * prm.ka(c) * dA;
     cc[2 * c + 1] = 2.0 * prm.kp(c) * dP;
@@ -86,13 +102,26 @@ __global__ void k_na_cells(const int32_t* he, const int32_t* face_he, const int3
 }
 
 // Out-half-edge slots per vertex; the counters start at zero (cleared by the
-// caller of this kernel on the same stream).
-__global__ void k_na_slots(const int32_t* he, int HE, int32_t* cnt, int32_t* slots) {
+// caller of this kernel on the same stream).  A source index out of range
+// sets kBadIndex and is not counted.
+__global__ void k_na_slots(const int32_t* he, int HE, int V, int32_t* cnt, int32_t* slots,
+                           int* bad) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= HE) return;
   const int s = he[8 * h + 3];
+  if (s < 0 || s >= V) {
+    atomicOr(bad, kBadIndex);
+    return;
+  }
   const int k = atomicAdd(&cnt[s], 1);
   if (k < 3) slots[3 * s + k] = h;
+}
+
+// kBadValence when a vertex is not the source of exactly three half-edges
+// (run on every call, whether or not forces are asked for).
+__global__ void k_na_valence(const int32_t* cnt, int V, int* bad) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < V && cnt[s] != 3) atomicOr(bad, kBadValence);
 }
 
 __device__ __forceinline__ void edge_d(const int32_t* he, int h, const double* X, double Lx,
@@ -105,15 +134,15 @@ __device__ __forceinline__ void edge_d(const int32_t* he, int h, const double* X
 // F_s = sum over the out-half-edges h of s (taken in increasing index, so
 // the sum is deterministic) of (Lambda_e + cP_f + cP_f') u_h
 // - 1/2 cA_f rot(d_h + d_prev(h)), f = face(h), f' = face(twin(h)).
-__global__ void k_na_vertices(const int32_t* he, const int32_t* edge_id, int V, double Lx,
+// A vertex that is not 3-valent, or whose tables hold an index out of
+// range, gets no force (its status bit is set by k_na_valence, or here).
+__global__ void k_na_vertices(const int32_t* he, const int32_t* edge_id, int n, double Lx,
                               double Ly, const double* X, ParamsD prm, const double* cc,
                               const int32_t* cnt, const int32_t* slots, double* F, int* bad) {
+  const int V = 2 * n, HE = 6 * n, E = 3 * n;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  if (cnt[s] != 3) {
-    atomicOr(bad, 1);
-    return;
-  }
+  if (cnt[s] != 3) return;
   int hs[3] = {slots[3 * s], slots[3 * s + 1], slots[3 * s + 2]};
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2 - i; ++j)
@@ -122,16 +151,27 @@ __global__ void k_na_vertices(const int32_t* he, const int32_t* edge_id, int V, 
         hs[j] = hs[j + 1];
         hs[j + 1] = t;
       }
+  auto in = [](int x, int m) { return x >= 0 && x < m; };
   double fx = 0, fy = 0;
   for (int k = 0; k < 3; ++k) {
     const int h = hs[k];
     const int32_t* r = he + 8 * h;
+    const int hp = r[0], tw = r[2], eid = edge_id[h];
+    bool ok = in(hp, HE) && in(tw, HE) && in(eid, E) && in(r[4], V) && in(r[5], n);
+    if (ok) {
+      const int32_t* rp = he + 8 * hp;
+      ok = in(rp[3], V) && in(rp[4], V) && in(he[8 * tw + 5], n);
+    }
+    if (!ok) {
+      atomicOr(bad, kBadIndex);
+      return;
+    }
     double dx, dy, px, py;
     edge_d(he, h, X, Lx, Ly, dx, dy);
-    edge_d(he, r[0], X, Lx, Ly, px, py);
+    edge_d(he, hp, X, Lx, Ly, px, py);
     const double l = sqrt(dx * dx + dy * dy);
-    const int f = r[5], f2 = he[8 * r[2] + 5];
-    const double T = prm.la(edge_id[h]) + cc[2 * f + 1] + cc[2 * f2 + 1];
+    const int f = r[5], f2 = he[8 * tw + 5];
+    const double T = prm.la(eid) + cc[2 * f + 1] + cc[2 * f2 + 1];
     fx += T * dx / l;
     fy += T * dy / l;
     const double wx = dx + px, wy = dy + py;  // r_next - r_prev
@@ -219,10 +259,11 @@ extern "C" vx_status vx_energy_forces_noalloc(const int32_t* he, const int32_t* 
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * V, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e == cudaSuccess) {
-    vx::k_na_cells<<<nbc, T, 0, s>>>(he, face_he, edge_id, n, Lx, Ly, X, prm, scratch);
-    vx::k_na_slots<<<(HE + T - 1) / T, T, 0, s>>>(he, HE, cnt, slots);
+    vx::k_na_slots<<<(HE + T - 1) / T, T, 0, s>>>(he, HE, V, cnt, slots, status);
+    vx::k_na_valence<<<(V + T - 1) / T, T, 0, s>>>(cnt, V, status);
+    vx::k_na_cells<<<nbc, T, 0, s>>>(he, face_he, edge_id, n, Lx, Ly, X, prm, scratch, status);
     if (F)
-      vx::k_na_vertices<<<(V + T - 1) / T, T, 0, s>>>(he, edge_id, V, Lx, Ly, X, prm, cc, cnt,
+      vx::k_na_vertices<<<(V + T - 1) / T, T, 0, s>>>(he, edge_id, n, Lx, Ly, X, prm, cc, cnt,
                                                        slots, F, status);
     if (E) vx::k_na_energy<<<1, 32, 0, s>>>(part, nbc, E);
     e = cudaGetLastError();

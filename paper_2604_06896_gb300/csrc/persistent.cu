@@ -316,10 +316,33 @@ static PersistArgs make_args(vx_tissue_s* t, const double* Xin, double* Xout, co
   return a;
 }
 
+// Kernels whose attributes were set (and, for clusters, whose occupancy was
+// checked) on a device: done once, so that a later call recorded in a CUDA
+// graph enqueues launches only.
+static std::mutex g_cfg_mu;
+static std::vector<std::pair<const void*, int>> g_cfg_done;
+static bool configured(const void* k) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  for (const auto& x : g_cfg_done)
+    if (x.first == k && x.second == dev) return true;
+  return false;
+}
+static void mark_configured(const void* k) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  g_cfg_done.emplace_back(k, dev);
+}
+
 template <class K>
 static cudaError_t launch_res(K kernel, int T, size_t smem, const PersistArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-  if (e != cudaSuccess) return e;
+  if (!configured((const void*)kernel)) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    if (e != cudaSuccess) return e;
+    mark_configured((const void*)kernel);
+  }
   kernel<<<1, T, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -350,7 +373,9 @@ static cudaError_t dispatch_res(vx_tissue_s* t, const PersistArgs& a, cudaStream
 
 template <class K>
 static cudaError_t launch_cluster(K kernel, const PersistArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const bool ready = configured((const void*)kernel);
+  cudaError_t e = cudaSuccess;
+  if (!ready) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterNR, 1, 1);
@@ -364,10 +389,13 @@ static cudaError_t launch_cluster(K kernel, const PersistArgs& a, cudaStream_t s
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int nclusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
-  if (e != cudaSuccess) return e;
-  if (nclusters < 1) return cudaErrorInvalidConfiguration;
+  if (!ready) {
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    mark_configured((const void*)kernel);
+  }
   return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
@@ -421,6 +449,34 @@ static int choose_path(vx_tissue_s* t, int path, bool adjoint) {
   return path;
 }
 
+vx_status minimize_launch(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
+                          int path, MinOut* out_dev, int* path_used, cudaStream_t s) {
+  const int p = choose_path(t, path, false);
+  if (p != VX_PATH_RESIDENT && p != VX_PATH_CLUSTER) {
+    set_error("without a host synchronisation only the resident and cluster paths can run "
+              "this tissue");
+    return VX_ERR_INVALID_ARG;
+  }
+  *path_used = p;
+  const bool f64 = t->dtype == VX_F64;
+  PersistArgs a = make_args(t, X, X, prm);
+  a.mp = mp;
+  a.out = out_dev;
+  cudaError_t e;
+  if (p == VX_PATH_RESIDENT) {
+    e = f64 ? dispatch_res<PolF64, false>(t, a, s) : dispatch_res<PolF32, false>(t, a, s);
+    if (e == cudaSuccess && mp.l_min > 0 && !mp.wrap) e = rebuild_flat(t, s);
+  } else {
+    e = f64 ? dispatch_cluster<PolF64, false>(t, a, s) : dispatch_cluster<PolF32, false>(t, a, s);
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("persistent minimiser launch: ") + cudaGetErrorString(e));
+    return VX_ERR_CUDA;
+  }
+  if (mp.wrap && wrap_tissue(t, X, &out_dev->wrap_err, s) != VX_OK) return VX_ERR_CUDA;
+  return VX_OK;
+}
+
 vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
                    int check_every, MinOut* out, int* path_used, cudaStream_t s) {
   const int p = choose_path(t, path, false);
@@ -444,7 +500,7 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
   cudaError_t e;
   if (p == VX_PATH_RESIDENT) {
     e = f64 ? dispatch_res<PolF64, false>(t, a, s) : dispatch_res<PolF32, false>(t, a, s);
-    if (e == cudaSuccess && mp.l_min > 0) e = rebuild_flat(t, s);
+    if (e == cudaSuccess && mp.l_min > 0 && !mp.wrap) e = rebuild_flat(t, s);
   } else {
     e = f64 ? dispatch_cluster<PolF64, false>(t, a, s) : dispatch_cluster<PolF32, false>(t, a, s);
   }
@@ -452,6 +508,7 @@ vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParam
     set_error(std::string("persistent minimiser launch: ") + cudaGetErrorString(e));
     return VX_ERR_CUDA;
   }
+  if (mp.wrap && wrap_tissue(t, X, &t->dout->wrap_err, s) != VX_OK) return VX_ERR_CUDA;
   if (cudaMemcpyAsync(out, t->dout, sizeof(MinOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error(std::string("vx_minimize: ") + cudaGetErrorString(cudaGetLastError()));
@@ -695,9 +752,12 @@ vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, co
             : launch_cluster_many<PolF32>(clu, d_args + ares.size(), s);
   if (e == cudaSuccess && !res.empty())
     e = f64 ? launch_res_many<PolF64>(res, d_args, s) : launch_res_many<PolF32>(res, d_args, s);
-  if (e == cudaSuccess && mp.l_min > 0)
+  if (e == cudaSuccess && mp.l_min > 0 && !mp.wrap)
     for (vx_tissue_s* t : res)
       if (e == cudaSuccess) e = rebuild_flat(t, s);
+  if (e == cudaSuccess && mp.wrap)
+    for (int k = 0; k < count; ++k)
+      if (wrap_tissue(ts[k], Xs[k], &d_out[k].wrap_err, s) != VX_OK) return VX_ERR_CUDA;
   if (e == cudaSuccess) e = cudaMemcpyAsync(outs, d_out, nargs * sizeof(MinOut), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -707,30 +767,23 @@ vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, co
   return VX_OK;
 }
 
+// The persistent adjoint.  The kernel writes its result to out_dev (the
+// tissue's result block when NULL); with out_host it is then copied there
+// and the stream synchronised, without it the call returns at once.
 vx_status adjoint_solve(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
-                        int path, AdjOut* out, cudaStream_t s) {
+                        int path, AdjOut* out_host, AdjOut* out_dev, cudaStream_t s) {
   const int p = choose_path(t, path, true);
   if (p < 0) {
     set_error("the tissue is too large for the adjoint kernels");
     return VX_ERR_INVALID_ARG;
   }
+  if (!out_dev) out_dev = (AdjOut*)t->dout;
   PersistArgs a = make_args(t, Xstar, nullptr, prm);
   a.ap = ap;
-  if (p == VX_PATH_CLUSTER) {
-    // per-cell 4-vectors in the workspace
-    const size_t need = 4 * (size_t)t->n + 64;
-    if (t->work_doubles < need + 4 * (size_t)t->V) {
-      if (t->work) cudaFree(t->work);
-      t->work = nullptr;
-      t->work_doubles = 0;
-      if (cudaMalloc(&t->work, 8 * (need + 4 * (size_t)t->V)) != cudaSuccess) {
-        set_error("out of device memory for the adjoint workspace");
-        return VX_ERR_OOM;
-      }
-      t->work_doubles = need + 4 * (size_t)t->V;
-    }
-    a.cell = t->work;
-  }
+  a.aout = out_dev;
+  // per-cell 4-vectors of the cluster path in the solver region of the
+  // workspace (4 n doubles)
+  if (p == VX_PATH_CLUSTER) a.cell = t->work;
   const bool f64 = t->dtype == VX_F64;
   cudaError_t e;
   if (p == VX_PATH_RESIDENT)
@@ -741,7 +794,8 @@ vx_status adjoint_solve(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
     set_error(std::string("adjoint launch: ") + cudaGetErrorString(e));
     return VX_ERR_CUDA;
   }
-  if (cudaMemcpyAsync(out, t->dout, sizeof(AdjOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (!out_host) return VX_OK;
+  if (cudaMemcpyAsync(out_host, out_dev, sizeof(AdjOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     set_error(std::string("adjoint: ") + cudaGetErrorString(cudaGetLastError()));
     return VX_ERR_CUDA;

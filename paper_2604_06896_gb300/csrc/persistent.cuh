@@ -54,6 +54,85 @@ __device__ __forceinline__ void v2v_grad(const View<P>& v, int i, const double* 
   gy = dy / v.V;
 }
 
+// Mean cell-shape-tensor anisotropy (the inverse-design outer cost):
+// S_c = (1/k) sum (r_i - c)(r_i - c)^T over the k corners of cell c (c their
+// mean), Q = mean_c S_c, q = ((Qxx - Qyy)/tr Q, 2 Qxy/tr Q),
+// C = |q - q_target|^2.  Per cell, the centroid (absolute, FP64) and k go to
+// `cent` / `kk`; the cell's S is returned (FP64 whatever the tissue's
+// precision: the cost is a small nudge on top of the forces).
+template <class P>
+__device__ __forceinline__ void cell_shape(const View<P>& v, int c, double2* cent, int* kk,
+                                           double& sxx, double& syy, double& sxy) {
+  const int h0 = v.ffirst[c];
+  const double2 X0 = P::to_d(v.X[src_of(v, h0)]);
+  double qx[kMaxCorners], qy[kMaxCorners];
+  int m = 0, cx = 0, cy = 0, h = h0;
+  qx[0] = 0;
+  qy[0] = 0;
+  do {
+    const uint32_t tg = v.tgt[h];
+    cx += tgt_ox(tg);
+    cy += tgt_oy(tg);
+    h = v.nxt[h];
+    ++m;
+    if (h != h0 && m < kMaxCorners) {
+      const double2 Xt = P::to_d(v.X[tgt_v(tg)]);
+      qx[m] = (Xt.x + cx * v.Lx) - X0.x;
+      qy[m] = (Xt.y + cy * v.Ly) - X0.y;
+    }
+  } while (h != h0 && m < kMaxCorners);
+  double mx = 0, my = 0;
+  for (int k = 0; k < m; ++k) {
+    mx += qx[k];
+    my += qy[k];
+  }
+  mx /= m;
+  my /= m;
+  sxx = syy = sxy = 0;
+  for (int k = 0; k < m; ++k) {
+    const double wx = qx[k] - mx, wy = qy[k] - my;
+    sxx += wx * wx;
+    syy += wy * wy;
+    sxy += wx * wy;
+  }
+  sxx /= m;
+  syy /= m;
+  sxy /= m;
+  cent[c] = make_double2(X0.x + mx, X0.y + my);
+  kk[c] = m;
+}
+
+// dC/dQ = (Gxx, Gyy, Gxy) from Q = (Qxx, Qyy, Qxy) and q_target.
+__device__ __forceinline__ void aniso_dC_dQ(const double (&Q)[3], const double* qt,
+                                            double (&G)[3]) {
+  const double T = Q[0] + Q[1];
+  const double q1 = (Q[0] - Q[1]) / T, q2 = 2.0 * Q[2] / T;
+  const double r1 = 2.0 * (q1 - qt[0]), r2 = 2.0 * (q2 - qt[1]);
+  G[0] = r1 * 2.0 * Q[1] / (T * T) - r2 * 2.0 * Q[2] / (T * T);
+  G[1] = -r1 * 2.0 * Q[0] / (T * T) - r2 * 2.0 * Q[2] / (T * T);
+  G[2] = r2 * 2.0 / T;
+}
+
+// dC/dx_i = sum over the three cells c of i of (1/(n k_c)) (2 Gxx wx + Gxy wy,
+// 2 Gyy wy + Gxy wx), w = x_i - centroid_c (minimum image).
+template <class P>
+__device__ __forceinline__ void aniso_grad_vertex(const View<P>& v, int i, const double2* cent,
+                                                  const int* kk, const double (&G)[3], double& gx,
+                                                  double& gy) {
+  const double2 x = P::to_d(v.X[i]);
+  gx = gy = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int c = v.vfc ? v.vfc[a * v.V + i] : v.face[v.vout[a * v.V + i]];
+    double wx = x.x - cent[c].x, wy = x.y - cent[c].y;
+    wx -= v.Lx * rint(wx / v.Lx);
+    wy -= v.Ly * rint(wy / v.Ly);
+    const double s = 1.0 / ((double)v.n * kk[c]);
+    gx += s * (2.0 * G[0] * wx + G[2] * wy);
+    gy += s * (2.0 * G[1] * wy + G[2] * wx);
+  }
+}
+
 // --------------------------------------------------------------- minimiser
 
 // Coefficients (cA, cP) of the listed cells, by the 32 lanes of one warp,
@@ -102,6 +181,7 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
   // centroid is conserved because every force term sums to zero).
   double nmx = 0, nmy = 0;
   const bool nudged = mp.cost == 1 && mp.nudge_s != 0.0;
+  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr;
   if (nudged) {
     double s2[2] = {0, 0};
 #pragma unroll
@@ -150,7 +230,7 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
           T1Stats s1 = {0, 0, 0};
           int nd = 0;
           t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1, sl.dirty, sl.dirty_cap,
-                       sl.dirty ? &nd : nullptr);
+                       sl.dirty ? &nd : nullptr, mp.edge_events);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
           nd = __shfl_sync(0xffffffffu, nd, 0);
@@ -176,6 +256,28 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     } else {
       tm.sync();
     }
+    // Anisotropy nudging: the cells' centroids and shape tensors, then
+    // dC/dQ from the team-wide mean Q (the reduction's barrier publishes the
+    // centroids to the whole team; the nudged phases run without T1, so
+    // bank c is free here).
+    double G[3] = {0, 0, 0};
+    if (nudged_aniso) {
+      double2* cent = (double2*)mp.aniso_ws;
+      int* kk = (int*)(mp.aniso_ws + 2 * (size_t)n);
+      double Q[3] = {0, 0, 0};
+      for (int c = f0; c < n; c += st) {
+        double sxx, syy, sxy;
+        cell_shape(vw, c, cent, kk, sxx, syy, sxy);
+        Q[0] += sxx;
+        Q[1] += syy;
+        Q[2] += sxy;
+      }
+      tm.template reduce<3>(Q, sl.c, 0);
+      Q[0] /= n;
+      Q[1] /= n;
+      Q[2] /= n;
+      aniso_dC_dQ(Q, mp.cost_data, G);
+    }
     // F.F, F.v, v.v, max |F_i|^2: FP32 tissues sum their per-thread and
     // per-warp parts in FP32 and combine warps in FP64
     constexpr bool kF32 = std::is_same<R, float>::value;
@@ -195,6 +297,14 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
           v2v_grad(vw, i, mp.cost_data, gx, gy);
           fx[k] -= (R)(mp.nudge_s * (gx - nmx));
           fy[k] -= (R)(mp.nudge_s * (gy - nmy));
+        }
+        if (nudged_aniso) {
+          // sum_i dC/dx_i = 0 (each cell's w sum to zero): no projection
+          double gx, gy;
+          aniso_grad_vertex(vw, i, (const double2*)mp.aniso_ws,
+                            (const int*)(mp.aniso_ws + 2 * (size_t)n), G, gx, gy);
+          fx[k] -= (R)(mp.nudge_s * gx);
+          fy[k] -= (R)(mp.nudge_s * gy);
         }
         if constexpr (kF32) {
           const float f2 = fx[k] * fx[k] + fy[k] * fy[k];
@@ -310,7 +420,7 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     o.n_short = (int)fin[2];
     o.n_inverted = (int)fin[1];
     o.force_evals = it + 1;
-    o.pad = 0;
+    o.wrap_err = 0;
     o.fmax = fmx;
     o.energy = fin[0];
     *out = o;
@@ -764,7 +874,8 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
       if (__syncthreads_or(fl)) {
         if (tid < 32) {
           T1Stats s1 = {0, 0, 0};
-          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1);
+          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, nullptr,
+                       mp.edge_events);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
         }
@@ -879,7 +990,7 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     o.n_short = (int)fin[2];
     o.n_inverted = (int)fin[1];
     o.force_evals = it + 1;
-    o.pad = 0;
+    o.wrap_err = 0;
     o.fmax = fmx;
     o.energy = fin[0];
     *out = o;

@@ -211,8 +211,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Called by one thread per CTA; false when the team aborted.
-__device__ __forceinline__ bool grid_arrive_wait(GridBar* b, unsigned m) {
+// Called by one thread per CTA; false when the team aborted (this CTA or
+// another waited longer than wait_ns).
+__device__ __forceinline__ bool grid_arrive_wait(GridBar* b, unsigned m,
+                                                 unsigned long long wait_ns = kGridWaitNs) {
   const unsigned g = ld_relaxed_gpu(&b->gen);
   if (atom_add_acq_rel_gpu(&b->count, 1u) == m - 1) {
     st_relaxed_gpu(&b->count, 0u);
@@ -223,7 +225,7 @@ __device__ __forceinline__ bool grid_arrive_wait(GridBar* b, unsigned m) {
   for (unsigned k = 0;; ++k) {
     if (ld_acquire_gpu(&b->gen) != g) return true;
     if (ld_relaxed_gpu(&b->abort)) return false;
-    if ((k & 63u) == 63u && global_ns() - t0 > kGridWaitNs) {
+    if ((k & 63u) == 63u && global_ns() - t0 > wait_ns) {
       st_relaxed_gpu(&b->abort, 1u);
       return false;
     }

@@ -41,13 +41,40 @@ struct vx_tissue_s {
   // adjoint workspace (float64 vectors [V][2] and per-cell sums)
   double* work;
   size_t work_doubles;
+  // image shifts of the exit-time wrap [V]
+  int2* wrapk;
 };
 
 namespace vx {
+// The float64 workspace `work`, allocated once by vx_tissue_create, in three
+// regions that calls use at the same time without overlap:
+//   solver: CG vectors of the plain adjoint (x, r, p, h, 2x2 blocks), the
+//           per-cell 4-vectors of the persistent adjoint and of the
+//           Hessian-vector product, partial sums and control words;
+//   ep:     the two nudged equilibria of equilibrium propagation, the cost
+//           and the two phases' results;
+//   aniso:  grad_X C of the anisotropy cost and its per-cell scratch.
+inline size_t work_solver_doubles(int n, int V) {
+  return 12 * (size_t)V + 4 * (size_t)n + 3 * (size_t)((V + 255) / 256) + 128;
+}
+inline size_t work_ep_doubles(int V) { return 4 * (size_t)V + 64; }
+inline size_t work_aniso_doubles(int n, int V) {
+  return 2 * (size_t)V + 3 * (size_t)n + 3 * (size_t)((n + 255) / 256) + 64;
+}
+inline size_t work_total_doubles(int n, int V) {
+  return work_solver_doubles(n, V) + work_ep_doubles(V) + work_aniso_doubles(n, V);
+}
+inline double* work_ep(vx_tissue_s* t) { return t->work + work_solver_doubles(t->n, t->V); }
+inline double* work_aniso(vx_tissue_s* t) { return work_ep(t) + work_ep_doubles(t->V); }
+
 vx_status energy_forces(vx_tissue_s* t, const double* X, const ParamsD& prm, double* F, double* E,
                         cudaStream_t s);
 vx_status minimize(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp, int path,
                    int check_every, MinOut* out, int* path_used, cudaStream_t s);
+// Exit-time wrap of X (device [V][2]) and of the tissue's offsets; an
+// offset that would leave {-1, 0, 1} sets *status_dev to VX_ERR_TOPOLOGY
+// (the slot is cleared first).  Rebuilds the flat tables.
+vx_status wrap_tissue(vx_tissue_s* t, double* X, int* status_dev, cudaStream_t s);
 size_t resident_smem_bytes(vx_tissue_s* t);
 vx_status minimize_many(vx_tissue_s* const* ts, int count, double* const* Xs, const ParamsD* prms,
                         const MinParams& mp, int path, MinOut* outs, int* paths, cudaStream_t s);
@@ -59,6 +86,14 @@ vx_status hessian_vector(vx_tissue_s* t, const double* X, const ParamsD& prm, co
 vx_status equilibrium_grad(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
                            const double* dCdX, const vx_grad_opts* o, double* g_lambda, double* g_A0,
                            double* g_P0, vx_grad_result* r, cudaStream_t s);
+// r_host: synchronous (result to the host); r_dev: asynchronous (the GPU
+// writes the result), exactly one of them non-NULL.
+vx_status equilibrium_grad_impl(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
+                                const double* dCdX, const vx_grad_opts* o, double* g_lambda,
+                                double* g_A0, double* g_P0, vx_grad_result* r_host,
+                                vx_grad_result* r_dev, cudaStream_t s);
+vx_status minimize_launch(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
+                          int path, MinOut* out_dev, int* path_used, cudaStream_t s);
 size_t aniso_scratch_doubles(int n);
 vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double* gradX,
                           double* scratch, double* C, cudaStream_t s);

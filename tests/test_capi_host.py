@@ -65,13 +65,35 @@ def test_mesh_bit_exact_many_seed_sets(vx):
             got = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
         except vx.VxError:
             got = None
-        if ref is None or got is None:
+        # both sides reject the same (degenerate) seed sets
+        assert (ref is None) == (got is None), (k, n, ref is None, got is None)
+        if ref is None:
             rejected += 1
             continue
         assert np.array_equal(got["he"], ref["he"]), (k, n)
         assert np.array_equal(got["edge_id"], ref["edge_id"])
         agree += 1
     assert agree > 700
+
+
+@pytest.mark.parametrize("case", ["c2", "c2_hilbert", "n5000"])
+def test_mesh_bit_exact_full_size(vx, case):
+    """The 10,000-cell tissue the benchmark builds (in the given seed order
+    and in Hilbert order, as the benchmark does) and a 5,000-cell tissue."""
+    if case.startswith("c2"):
+        c = vi.tissue_c2(3.7)
+        seeds = c["seeds"]
+        if case == "c2_hilbert":
+            seeds = seeds[vx.vx_seed_order(seeds, c["Lx"], c["Ly"])]
+    else:
+        c = vi.small_tissue(5000, 69)
+        seeds = c["seeds"]
+    got = vx.vx_build_mesh(seeds, c["Lx"], c["Ly"])
+    ref = omesh.build_periodic_voronoi(seeds, c["Lx"], c["Ly"])
+    assert np.array_equal(got["he"], ref["he"])
+    assert np.array_equal(got["face_he"], ref["face_he"])
+    assert np.array_equal(got["edge_id"], ref["edge_id"])
+    assert np.abs(got["vert"] - ref["vert"]).max() < 1e-12 * max(c["Lx"], c["Ly"])
 
 
 def test_mesh_c1_and_honeycomb(vx):

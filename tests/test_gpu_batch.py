@@ -38,7 +38,7 @@ def test_batch_fp64_matches_oracle(vx):
     lam = np.concatenate([c["lam"] for c, _ in ts])
     params = dict(KA=1.0, KP=1.0, A0=1.0, P0=np.array(p0s), lam=torch.tensor(lam, device="cuda"))
     rs = vx.vx_minimize_batched(b, X, params, tol=1e-9, max_iter=50000, dt0=0.01, dt_max=0.5,
-                                l_min=5e-3)
+                                l_min=5e-3, wrap=0)
     tops = b.topologies()
     Xs = b.split(X.cpu().numpy())
     for k, ((c, m), r) in enumerate(zip(ts, rs)):

@@ -87,8 +87,10 @@ def test_c4_adjoint_vs_oracle_ep_fd(vx, c4):
             l2 = lam.copy()
             l2[e_] += sgn * h
             X = torch.tensor(Xs, dtype=torch.float64, device="cuda")
+            # every re-minimisation starts from X* on the same tissue: no wrap,
+            # so the tissue's offsets stay those of X*
             r = vx.vx_minimize(t, X, dict(base, lam=l2), tol=1e-12, max_iter=200000, dt0=0.01,
-                               dt_max=0.5)
+                               dt_max=0.5, wrap=0)
             assert r.converged
             vals.append(omodel.cost_v2v(X.cpu().numpy(), Xtgt, top)[0])
         fd.append((vals[0] - vals[1]) / (2 * h))
@@ -97,3 +99,59 @@ def test_c4_adjoint_vs_oracle_ep_fd(vx, c4):
     print(f"c4 FD on 20 edges: max rel err {e:.2e}")
     assert e < 1e-4
     t.close()
+
+
+@pytest.fixture(scope="module")
+def c4_oracle():
+    """The parameter-inference workload run by the oracle alone (FP64, T1
+    on): the target equilibrium under the hidden tensions from the Voronoi
+    state, the trial equilibrium under the trial tensions from the target,
+    and the adjoint gradient of the v2v cost there."""
+    c = vi.tissue_c4()
+    t = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    base = dict(KA=c["KA"], KP=c["KP"], A0=c["A0"], P0=c["P0"])
+    o = osolv.MinOpts(tol=1e-10, max_iter=100000, dt0=0.01, dt_max=0.5)
+    tgt = osolv.relax(t["vert"], t, dict(base, lam=c["lam_hidden"]), o, l_min=5e-3)
+    trial = osolv.relax(tgt.X, tgt.tissue, dict(base, lam=c["lam"]), o, l_min=5e-3)
+    assert tgt.converged and trial.converged
+    top = dict(trial.tissue, vert=trial.X)
+    C, G = omodel.cost_v2v(trial.X, tgt.X, top)
+    g_ref, _, info = osolv.adjoint_grad(trial.X, top, dict(base, lam=c["lam"]), G)
+    assert info["pd"]
+    return c, base, dict(tgt.tissue, vert=tgt.X), top, g_ref, C
+
+
+def test_c4_fp32_pipeline_vs_oracle(vx, c4_oracle):
+    """The benchmarked gradient solve end to end in FP32: an FP32 tissue at
+    the target's topology relaxes from the target equilibrium under the
+    trial tensions to max|F| < 1e-5 sqrt(A0) (cluster path), then the FP32
+    adjoint (CG to rtol 1e-6) gives the gradient with respect to the 3,000
+    tensions.  Against the oracle's FP64 pipeline on the same inputs: same
+    T1 decisions (same topology), the equilibrium and the gradient errors
+    are printed and bounded.  The gradient error is set by the relaxation
+    tolerance: an equilibrium known to max|F| ~ tol is off by ~ tol /
+    lambda_min along the softest mode, and the v2v gradient is linear in
+    X* - X_target (the errors at the benchmark's tolerance and at the FP32
+    floor are both reported)."""
+    import torch
+    c, base, tgt, top_ref, g_ref, C_ref = c4_oracle
+    p = dict(base, lam=c["lam"])
+    Xt = torch.tensor(tgt["vert"], dtype=torch.float64, device="cuda")
+    out = {}
+    for tol in (1e-5, 2e-6):
+        t = vx.Tissue(tgt, "f32")
+        X = Xt.clone()
+        r = vx.vx_minimize(t, X, p, tol=tol, max_iter=100000, dt0=0.01, dt_max=0.5, l_min=5e-3,
+                           path="cluster", wrap=0)
+        top = t.topology()
+        g, rg = vx.vx_equilibrium_grad(t, X, p, cost=vx.VX_COST_V2V, cost_data=Xt, cg_rtol=1e-6)
+        ex = np.abs(X.cpu().numpy() - top_ref["vert"]).max()
+        eg = rel(g["lam"].cpu().numpy(), g_ref["lam"])
+        out[tol] = (ex, eg)
+        print(f"c4 FP32 pipeline tol {tol:.0e}: status {r.status} {r.iters} it {r.n_t1} T1, "
+              f"|X - X_oracle| {ex:.2e}, grad vs oracle {eg:.2e}, C {rg.cost:.6e} vs {C_ref:.6e}")
+        assert r.converged and rg.status == 0
+        assert np.array_equal(top["he"], top_ref["he"])
+        t.close()
+    assert out[1e-5][1] < 5e-2
+    assert out[2e-6][1] < 1e-2
