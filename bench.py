@@ -30,12 +30,17 @@ import vx_inputs as vi  # noqa: E402
 
 METRIC = "vertex-force evals/s & equilibrium-gradient solves/s vs plain GPU path at tol"
 UNIT = "vertex-force evals/s"
-WORKLOAD = "c2: 10,000-cell periodic Voronoi tissue, FIRE+T1 to max|F|<1e-6*sqrt(A0), p0 in {3.5,3.7,3.9}"
+WORKLOAD = ("c2: 10,000-cell periodic Voronoi tissue (20,000 vertices), FP32 hi/lo positions, "
+            "FIRE+T1, p0 in {3.5,3.7,3.9}, tolerance 1e-6*sqrt(A0) with a 20,000-iteration budget "
+            "per relaxation (the tolerance is not reached: short edges keep being stretched)")
+MODULI = ("dimensionless moduli: K_A = 1/A0, K_P = 1, P0 = p0*sqrt(A0), Lambda = 0.05*sqrt(A0), "
+          "A0 = 1e-4, box 1 x 1")
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an
-# ncu capture of the current kernel
-TRAFFIC_BYTES = 10_277_120 + 105_472
+# ncu capture of the current kernel (None until the changed kernel is
+# captured again)
+TRAFFIC_BYTES = None
 MAX_ITER = 20_000   # per relaxation: a fixed budget (the tolerance is not reached)
 
 
@@ -123,6 +128,47 @@ def cpu_sample(seconds=12.0):
                        f"p0=3.7 tissue from its Voronoi state, numpy FP64, {dt:.1f} s")
 
 
+def _oracle_worker(job):
+    """One host process of the all-cores oracle sample: FIRE + T1 on the
+    10,000-cell tissue (p0 = job's), for about `seconds`."""
+    p0, seconds = job
+    from oracle import mesh as omesh
+    from oracle import solvers as osolv
+    c = vi.tissue_c2(p0)
+    t = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    o = opts_for(c["A0"], 0)
+    mo = osolv.MinOpts(tol=o["tol"], max_iter=3, dt0=o["dt0"], dt_max=o["dt_max"])
+    t0 = time.perf_counter()
+    r = osolv.relax(t["vert"], t, p, mo, l_min=o["l_min"])
+    per = (time.perf_counter() - t0) / (r.iters + 1)
+    mo.max_iter = max(3, int(seconds / per))
+    t0 = time.perf_counter()
+    r = osolv.relax(t["vert"], t, p, mo, l_min=o["l_min"])
+    return t["vert"].shape[0], r.iters + 1, time.perf_counter() - t0
+
+
+def cpu_sample_all_cores(seconds=15.0):
+    """The oracle on every host core at once: one process per core, each
+    relaxing the 10,000-cell tissue (the three p0 in turn) for about
+    `seconds`; value = sum of V x force evaluations / the longest process
+    time.  Processes are spawned (none is forked from a CUDA process)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    jobs = [(vi.C2_P0_SWEEP[k % 3], seconds) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    evals = sum(v * e for v, e, _ in res)
+    wall = max(d for _, _, d in res)
+    return dict(value=evals / wall, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{cores} processes, each {min(e for _, e, _ in res)}-"
+                       f"{max(e for _, e, _ in res)} FIRE+T1 iterations of the 10,000-cell tissue "
+                       f"from its Voronoi state (p0 = 3.5, 3.7, 3.9 in turn), numpy FP64, "
+                       f"{wall:.1f} s")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -132,7 +178,7 @@ def run_reference(args):
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        s = cpu_sample(seconds=max(5.0, 40.0 / max(1, args.steps)))
+        s = cpu_sample_all_cores(seconds=max(5.0, 40.0 / max(1, args.steps)))
         vals.append(s["value"])
     wall = time.perf_counter() - t_all
     value = float(np.mean(vals))
@@ -140,8 +186,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (bounded CPU sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD + " (bounded CPU sample on every host core)",
+                       "moduli": MODULI},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
                              "sample": s["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -151,12 +198,14 @@ def run_reference(args):
 # ------------------------------------------------------------------- GPU
 
 def algorithmic_bytes_per_iter(n):
-    """Bytes one FIRE iteration must touch if every array were streamed once
-    (FP32 path): positions hi/lo read + write (32 V), velocities read +
-    write (16 V), half-edge target/next/face (12 HE), vertex out-lists (12 V),
-    face starts (4 n), cell coefficients written and read (16 n)."""
-    V, HE = 2 * n, 6 * n
-    return 32 * V + 16 * V + 12 * HE + 12 * V + 4 * n + 16 * n
+    """Algorithmic bytes of one FIRE iteration of an n-cell tissue with
+    uniform tension and uniform per-cell parameters, FP32 positions: one
+    energy + force evaluation reads X (16 n: 2 n vertices x 8 B), writes F
+    (16 n) and reads the cell cycles (24 n: 6 n packed corner words); the
+    FIRE step reads and writes v (32 n) and writes X (16 n); the lo halves
+    of the hi/lo positions add 16 n to each of the two X streams:
+    56 n + 48 n + 32 n = 136 n."""
+    return 136 * n
 
 
 def grad_metric(vx, torch, steps, warmup):
@@ -192,7 +241,7 @@ def grad_metric(vx, torch, steps, warmup):
             r = vx.vx_minimize(t, X, p, **o)
             g, rg = vx.vx_equilibrium_grad(t, X, p, cost=vx.VX_COST_V2V, cost_data=Xt,
                                            cg_rtol=1e-6, inner=dict(path=path))
-            return r, rg
+            return r, rg, g
 
         for _ in range(warmup):
             solve()
@@ -205,7 +254,11 @@ def grad_metric(vx, torch, steps, warmup):
             b.record()
             b.synchronize()
             ms += a.elapsed_time(b)
-        r, rg = rs[-1]
+        r, rg, g = rs[-1]
+        if path == "auto":
+            # what the oracle check needs (the last solve's state)
+            check = dict(X=X.cpu().numpy(), top=t.topology(), g=g["lam"].cpu().numpy(),
+                         Xt=Xt.cpu().numpy(), p=p, fmax=r.fmax)
         out[path] = {"value": steps / (ms * 1e-3), "ms_per_solve": ms / steps,
                      "path": {1: "resident", 2: "plain", 3: "cluster", 4: "grid"}.get(r.path_used),
                      "min_status": r.status, "min_iters": r.iters, "n_t1": r.n_t1,
@@ -217,7 +270,177 @@ def grad_metric(vx, torch, steps, warmup):
                         "max|F|<1e-5*sqrt(A0) from the target equilibrium, then the adjoint "
                         "(CG to rtol 1e-6)",
             "value": out["auto"]["value"], "vs_plain_gpu_path": out["auto"]["value"] / out["plain"]["value"],
-            "persistent": out["auto"], "plain_gpu_path": out["plain"]}
+            "persistent": out["auto"], "plain_gpu_path": out["plain"]}, check
+
+
+def c4_oracle_errors(check):
+    """The oracle at the GPU's c4 result: its dense adjoint gradient at the
+    GPU's equilibrium and topology (the FP32 adjoint's error), and its
+    max |F| there (how far the FP32 equilibrium is from force balance)."""
+    from oracle import model as omodel
+    from oracle import solvers as osolv
+    top = dict(check["top"], vert=check["X"])
+    _, G = omodel.cost_v2v(check["X"], check["Xt"], top)
+    g_ref, _, info = osolv.adjoint_grad(check["X"], top, check["p"], G)
+    F = omodel.forces(check["X"], top, check["p"])
+    d = check["g"] - g_ref["lam"]
+    return {"adjoint_rel_error": float(np.linalg.norm(d) / np.linalg.norm(g_ref["lam"])),
+            "oracle_fmax_at_X": float(np.sqrt((F * F).sum(axis=1)).max()),
+            "gpu_fmax": check["fmax"], "hessian_pd": bool(info["pd"]),
+            "note": "oracle dense adjoint at the GPU's FP32 equilibrium and topology; the "
+                    "end-to-end error of the FP32 pipeline against the oracle's own FP64 "
+                    "pipeline is measured by tests/test_gpu_c4.py"}
+
+
+def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000):
+    """The batched forward workload: 512 periodic Voronoi tissues of
+    log-uniform size in [200, 5000] cells (7.5e5 cells in all), per-tissue
+    p0 ~ U(3.5, 4.0), per-edge Lambda ~ U(0, 0.1), FP32, FIRE + T1 to
+    max|F| < 1e-6 with a budget of max_iter iterations, in one persistent
+    graph-replayed launch (vx_minimize_batched).  Vertex-force evals/s
+    (L2 flushed before each timed step).  The plain GPU path (one launch per
+    sub-step, one tissue at a time) is too slow for the whole batch; it is
+    compared with the batched path on every subset_every-th tissue (the same
+    inputs and options for both)."""
+    batch = vi.batch_c3()
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
+    kw = dict(tol=1e-6, max_iter=max_iter, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def run_batched(idx, nsteps):
+        b = vx.Batch([meshes[k] for k in idx], "f32")
+        X0 = torch.tensor(np.concatenate([meshes[k]["vert"] for k in idx]), dtype=torch.float64,
+                          device="cuda")
+        lam = torch.tensor(np.concatenate([batch[k]["lam"] for k in idx]), device="cuda")
+        prm = dict(KA=1.0, KP=1.0, A0=1.0, P0=np.array([batch[k]["P0"] for k in idx]), lam=lam)
+        X = X0.clone()
+        vx.vx_minimize_batched(b, X, prm, **kw)      # capture + warm-up
+        ms, evals, rs = 0.0, 0, None
+        for _ in range(nsteps):
+            vx.vx_batch_restore(b)
+            X.copy_(X0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rs = vx.vx_minimize_batched(b, X, prm, **kw)
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            evals += sum(int(b.V[k]) * r.force_evals for k, r in enumerate(rs))
+        b.close()
+        return evals / (ms * 1e-3), ms / nsteps, rs
+
+    allidx = list(range(len(batch)))
+    value, ms_step, rs = run_batched(allidx, steps)
+    sub = allidx[::subset_every]
+    sub_value, sub_ms, _ = run_batched(sub, 1)
+    plain_ms, plain_evals = 0.0, 0
+    for k in sub:
+        c = batch[k]
+        t = vx.Tissue(meshes[k], "f32")
+        X = torch.tensor(meshes[k]["vert"], dtype=torch.float64, device="cuda")
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=c["P0"], lam=c["lam"])
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = vx.vx_minimize(t, X, p, path="plain", check_every=100, **kw)
+        e1.record()
+        e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        plain_evals += t.V * r.force_evals
+        t.close()
+    plain_value = plain_evals / (plain_ms * 1e-3)
+    ncells = sum(c["n"] for c in batch)
+    return {"metric": "vertex-force evals/s", "unit": "vertex-force evals/s", "value": value,
+            "ms_per_step": ms_step,
+            "workload": f"c3: {len(batch)} tissues, {ncells} cells (log-uniform 200-5000 per tissue), "
+                        f"p0 ~ U(3.5,4.0), Lambda ~ U(0,0.1), A0 = 1, FP32, FIRE+T1 to max|F|<1e-6, "
+                        f"{max_iter}-iteration budget, one graph-replayed persistent launch",
+            "converged": int(sum(r.status == 0 for r in rs)),
+            "force_evals_per_tissue": [int(min(r.force_evals for r in rs)),
+                                       int(max(r.force_evals for r in rs))],
+            "subset": {"tissues": len(sub), "batched_value": sub_value, "batched_ms": sub_ms,
+                       "plain_gpu_path_value": plain_value, "plain_gpu_path_ms": plain_ms,
+                       "vs_plain_gpu_path": sub_value / plain_value}}
+
+
+def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None):
+    """The batched inverse-design workload: 64 periodic Voronoi tissues of
+    10,000 cells (box 100, A0 = 1 per cell, Lambda ~ U(0, 0.1) per edge,
+    p0 = 3.7), FP32; one equilibrium-gradient solve = the free relaxation
+    (FIRE + T1, max|F| < 1e-6 or a budget of free_iters iterations) then the
+    adjoint gradient of the anisotropy cost (q_target = (0.1, 0)) with
+    respect to the per-cell A0 and per-edge Lambda (CG to rtol 1e-6, FP64
+    reductions).  Batched: every tissue in one graph-replayed persistent
+    launch (vx_batch_grad).  Plain GPU path: one tissue at a time, one launch
+    per sub-step for the relaxation and for the CG (host-polled), on the
+    same inputs and options.  Solves/s = tissues / wall time (CUDA events)."""
+    batch = vi.batch_c5()
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
+    free = dict(tol=1e-6, max_iter=free_iters, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    qt = np.array([0.1, 0.0])
+    b = vx.Batch(meshes, "f32")
+    X0 = torch.tensor(np.concatenate([m["vert"] for m in meshes]), dtype=torch.float64,
+                      device="cuda")
+    lam = torch.tensor(np.concatenate([c["lam"] for c in batch]), device="cuda")
+    A0 = torch.ones(int(b.n.sum()), dtype=torch.float64, device="cuda")
+    prm = dict(KA=1.0, KP=1.0, A0=A0, P0=3.7, lam=lam)
+    X = X0.clone()
+    vx.vx_batch_grad(b, X, prm, vx.VX_COST_ANISO, qt, what=1, free=free, cg_rtol=1e-6)  # capture
+    vx.vx_batch_restore(b)
+    X.copy_(X0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ga, _, rs = vx.vx_batch_grad(b, X, prm, vx.VX_COST_ANISO, qt, what=1, free=free, cg_rtol=1e-6)
+    e1.record()
+    e1.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    b.close()
+    idx = list(range(len(batch))) if plain_tissues is None else list(range(plain_tissues))
+    ms_p = 0.0
+    for k in idx:
+        c = batch[k]
+        t = vx.Tissue(meshes[k], "f32")
+        Xk = torch.tensor(meshes[k]["vert"], dtype=torch.float64, device="cuda")
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=c["lam"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vx.vx_minimize(t, Xk, p, path="plain", check_every=100, **free)
+        vx.vx_equilibrium_grad(t, Xk, p, cost=vx.VX_COST_ANISO, cost_data=qt, cg_rtol=1e-6,
+                               inner=dict(path="plain", check_every=20))
+        e1.record()
+        e1.synchronize()
+        ms_p += e0.elapsed_time(e1)
+        t.close()
+    v_b = len(batch) / (ms_b * 1e-3)
+    v_p = len(idx) / (ms_p * 1e-3)
+    return {"metric": "equilibrium-gradient solves/s", "unit": "solves/s", "value": v_b,
+            "ms_per_batch": ms_b,
+            "workload": f"c5: {len(batch)} tissues x 10,000 cells, FP32, FIRE+T1 to max|F|<1e-6 "
+                        f"({free_iters}-iteration budget), anisotropy cost, adjoint gradient for "
+                        f"per-cell A0 and per-edge Lambda (CG rtol 1e-6), one launch",
+            "free_converged": int(sum(r[0].status == 0 for r in rs)),
+            "cg_iters": [int(min(r[1].cg_iters for r in rs)), int(max(r[1].cg_iters for r in rs))],
+            "plain_gpu_path": {"value": v_p, "tissues": len(idx), "ms": ms_p},
+            "vs_plain_gpu_path": v_b / v_p}
+
+
+def c2_oracle_errors(finals):
+    """The oracle's energy and max |F| at each c2 relaxation's returned state
+    (GPU energy relative error, GPU max |F| against the oracle's)."""
+    from oracle import model as omodel
+    out = []
+    for p0, X, top, p, r in finals:
+        t = dict(top, vert=X)
+        E = omodel.energy(X, t, p)
+        F = omodel.forces(X, t, p)
+        out.append({"p0": p0, "energy_rel_error": abs(r.energy - E) / abs(E),
+                    "oracle_fmax": float(np.sqrt((F * F).sum(axis=1)).max()), "gpu_fmax": r.fmax})
+    return out
 
 
 def run_gpu(args):
@@ -348,12 +571,21 @@ def run_gpu(args):
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
+    # the returned state of each relaxation (for the oracle check)
+    finals = [(p0, cs[5].cpu().numpy(), cs[3].topology(), cs[2], r)
+              for p0, cs, r in zip(vi.C2_P0_SWEEP, cases, rs)]
 
-    grad = grad_metric(vx, torch, steps=max(1, args.steps), warmup=1)
+    grad, grad_check = grad_metric(vx, torch, steps=max(1, args.steps), warmup=1)
+    batched = None if args.no_batch else batched_forward_metric(vx, torch, steps=1)
+    batched_grad = None if args.no_batch else batched_gradient_metric(vx, torch)
 
-    cpu = None
+    # cpu_baseline leg: the oracle timed on the host cores, and the oracle
+    # checked against this run's results
+    cpu, oracle_errors = None, None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_sample(seconds=12.0)
+        cpu = cpu_sample_all_cores(seconds=15.0)
+        cpu["single_core"] = cpu_sample(seconds=12.0)
+        oracle_errors = {"c2": c2_oracle_errors(finals), "c4": c4_oracle_errors(grad_check)}
 
     if world > 1:
         dist.destroy_process_group()
@@ -364,7 +596,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_t.item() / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_cells": n, "n_vertices": V,
+        "config": {"workload": WORKLOAD, "moduli": MODULI, "n_cells": n, "n_vertices": V,
                    "numbering": "seeds in Hilbert-curve order (vx_seed_order)",
                    "path": {1: "resident", 2: "plain", 3: "cluster"}.get(path_used, path_used),
                    "l2": "flushed (256 MiB write) before every timed step",
@@ -377,21 +609,27 @@ def run_gpu(args):
         "converged": conv,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * V * 16,
                 "d2h_bytes_per_step": 3 * V * 16},
-        # per step: one k_rebuild_flat per tissue (vx_tissue_restore) and the
-        # one persistent minimiser launch
-        "gpu_launches": args.steps * (len(cases) + 1),
+        # per step: one k_rebuild_flat per tissue (vx_tissue_restore), the one
+        # persistent minimiser launch, and per tissue the exit-time wrap
+        # (k_wrap_pos, k_wrap_tgt, k_rebuild_flat)
+        "gpu_launches": args.steps * (len(cases) + 1 + 3 * len(cases)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": TRAFFIC_BYTES,
                      "kernel": "k_min_cluster_many (one persistent launch, one 16-CTA cluster per relaxation)",
-                     "note": "algorithmic bytes/iteration x iterations / launch time; the "
-                             "tissue state lives in L2, peak is the measured HBM copy rate; "
-                             "traffic = dram bytes read+written by one ncu capture of this "
-                             "kernel (300 iterations of the same three tissues): the state "
-                             "is loaded into L2 once, so it does not grow with iterations "
-                             "(profiles/k_min_cluster_many_c2.md)"},
+                     "bytes_per_iteration": "136 n (n = 10,000 cells): evaluation 56 n + FIRE "
+                                            "step 48 n + lo halves of the two X streams 32 n",
+                     "note": "algorithmic bytes per iteration x iterations / launch time, against "
+                             "the measured HBM copy rate (of measured); the tissue state (~2 MB "
+                             "per relaxation) stays in L2 and the kernel is bound by L2 latency "
+                             "and barriers, not by bandwidth; traffic (dram bytes read + written "
+                             "per launch, one ncu capture) is null until the changed kernel is "
+                             "captured again"},
         "equilibrium_gradient": grad,
+        "batched_forward": batched,
+        "batched_gradient": batched_grad,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "oracle_errors": oracle_errors,
     }
     print(json.dumps(line))
 
@@ -479,6 +717,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vx", choices=["vx", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched c3 line")
     ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
     ap.add_argument("--profile-iters", type=int, default=2000)
     ap.add_argument("--ordered", type=int, default=1, help="profile: Hilbert-ordered seeds")

@@ -66,7 +66,9 @@ typedef enum {
 
 enum { VX_F64 = 0, VX_F32 = 1 };
 enum { VX_FIRE = 0, VX_GD = 1 };
-enum { VX_ADJOINT_CG = 0, VX_EP_CENTERED = 1, VX_EP_FORWARD = 2 };
+enum { VX_ADJOINT_CG = 0, VX_EP_CENTERED = 1, VX_EP_FORWARD = 2, VX_ADJOINT_MINRES = 3 };
+/* Parameter kinds of vx_sensitivity_grad. */
+enum { VX_PARAM_LAMBDA = 0, VX_PARAM_A0 = 1, VX_PARAM_P0 = 2 };
 enum { VX_COST_NONE = 0, VX_COST_V2V = 1, VX_COST_ANISO = 2 };
 /* Execution paths of the persistent solvers:
  *   RESIDENT: one CTA holds the whole tissue in shared memory for the whole
@@ -300,6 +302,11 @@ void vx_grad_opts_default(vx_grad_opts* o);
  *   on a cluster), or, with o->inner.path = VX_PATH_PLAIN, as one launch per
  *   sub-step with FP64 vectors and the status polled every
  *   o->inner.check_every iterations (the reference GPU path).
+ * VX_ADJOINT_MINRES (Methods, "Implicit differentiation": Krylov solves for
+ *   Hessians that are not positive definite): the same adjoint with the
+ *   linear system solved by MINRES (Paige and Saunders 1975; no
+ *   preconditioner) on the plain path, for the indefinite Hessians on which
+ *   CG stops with VX_ERR_INDEFINITE.
  * VX_EP_CENTERED / VX_EP_FORWARD (Methods, "Equilibrium propagation"):
  *   re-minimise E +/- (beta/2) C (or E + beta C and the free X*) from X*,
  *   nudging with the translation-free part of grad_X C, and difference
@@ -314,6 +321,23 @@ vx_status vx_equilibrium_grad(vx_tissue t, const double* Xstar, const vx_params*
                               const double* dCdX, const vx_grad_opts* o,
                               double* g_lambda, double* g_A0, double* g_P0,
                               vx_grad_result* r, void* stream);
+
+/*
+ * vx_sensitivity_grad — the forward form of implicit differentiation
+ * (Methods, "Implicit differentiation", sensitivity form): for each listed
+ * parameter theta_k (kind[k] VX_PARAM_LAMBDA with index[k] an edge id,
+ * VX_PARAM_A0 / VX_PARAM_P0 with a cell), solve H s_k = d(grad_X E)/d theta_k
+ * (solver VX_ADJOINT_CG or VX_ADJOINT_MINRES, to rtol, on the plain path)
+ * and return dC/d theta_k = -grad_X C . s_k: one linear solve per
+ * parameter, the same numbers as the adjoint (which needs one solve for
+ * all).  Xstar, dCdX dev float64 [V][2]; kind, index host int32 [count];
+ * out host float64 [count]; status host int32 [count] or NULL (per solve
+ * VX_OK / VX_NOT_CONVERGED / VX_ERR_INDEFINITE).  Synchronises `stream`.
+ */
+vx_status vx_sensitivity_grad(vx_tissue t, const double* Xstar, const vx_params* p,
+                              const double* dCdX, int32_t count, const int32_t* kind,
+                              const int32_t* index, int32_t solver, double rtol, int32_t max_iter,
+                              double* out, int32_t* status, void* stream);
 
 /*
  * Asynchronous forms, for CUDA graphs.  Every call above that takes a
@@ -461,6 +485,37 @@ vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_
                                       const double* dCdX, double cg_rtol, int32_t cg_max_iter,
                                       double* g_lambda, double* g_A0, double* g_P0,
                                       vx_grad_result* r, void* stream);
+
+/*
+ * vx_batch_grad — the batched gradient workload in one persistent launch
+ * (replayed from a CUDA graph captured at the first call with these
+ * arguments): for every tissue of the batch, taken largest first by the
+ * CTAs of the launch, (1) the free relaxation from X to X* under
+ * free_opts (Methods, "Simulation engine", "T1 transitions"); (2) the
+ * built-in outer cost go->cost (VX_COST_V2V with go->cost_data = X_target
+ * dev [sum V][2], or VX_COST_ANISO with q_target dev [2]) and its gradient
+ * at X*; (3) with what & VX_GRAD_ADJOINT, the adjoint gradient (Methods,
+ * "Implicit differentiation": preconditioned CG to go->cg_rtol, FP64
+ * reductions); (4) with what & VX_GRAD_EP, equilibrium propagation
+ * (Methods, "Equilibrium propagation"): the nudged phases E +/- (beta/2) C
+ * (go->mode VX_EP_CENTERED) or E + beta C (VX_EP_FORWARD) from X* under
+ * go->inner without T1, in FP64 arithmetic when go->ep_f64, then the
+ * difference of d_theta E over beta.  X dev float64 [sum V][2] in/out
+ * (X*, wrapped per free_opts->wrap).  Gradients (each may be NULL): ga_*
+ * adjoint, ge_* EP; lambda dev [sum E], A0 and P0 dev [sum n].  r host
+ * [count] (out).  Nothing is allocated (the workspace is sized by
+ * vx_batch_create).  Synchronises `stream`.
+ */
+enum { VX_GRAD_ADJOINT = 1, VX_GRAD_EP = 2 };
+typedef struct {
+  vx_min_result free;      /* the free relaxation to X*                      */
+  vx_grad_result adjoint;  /* status, CG iterations, residual; cost at X*    */
+  vx_grad_result ep;       /* status, nudged iterations; cost at X*          */
+} vx_batch_grad_result;
+vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params* p,
+                        const vx_min_opts* free_opts, const vx_grad_opts* go, int32_t what,
+                        double* ga_lambda, double* ga_A0, double* ga_P0, double* ge_lambda,
+                        double* ge_A0, double* ge_P0, vx_batch_grad_result* r, void* stream);
 
 /*
  * vx_batch_aniso_cost — the anisotropy cost of every tissue (the batched

@@ -14,8 +14,9 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi as capi
-from ._capi import (VX_ADJOINT_CG, VX_COST_ANISO, VX_COST_NONE, VX_COST_V2V,  # noqa: F401
-                    VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
+from ._capi import (VX_ADJOINT_CG, VX_ADJOINT_MINRES, VX_COST_ANISO, VX_COST_NONE,  # noqa: F401
+                    VX_COST_V2V, VX_EP_CENTERED, VX_EP_FORWARD, VX_F32, VX_F64, VX_FIRE, VX_GD,
+                    VX_GRAD_ADJOINT, VX_GRAD_EP, VX_PARAM_A0, VX_PARAM_LAMBDA, VX_PARAM_P0,
                     VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_GRID, VX_PATH_PLAIN, VX_PATH_RESIDENT,
                     VxError)
 
@@ -362,6 +363,26 @@ def vx_equilibrium_grad(t: Tissue, Xstar, params, dCdX=None, mode=VX_ADJOINT_CG,
     return g, GradResult(r.status, r.cg_iters, r.cg_rel_residual, r.cost, tuple(r.nudged_iters))
 
 
+def vx_sensitivity_grad(t: Tissue, Xstar, params, dCdX, kinds, indices, solver=VX_ADJOINT_CG,
+                        rtol=1e-10, max_iter=20000):
+    """Forward-mode implicit differentiation (see vx.h): dC/dtheta for the
+    listed parameters (kinds: VX_PARAM_LAMBDA / A0 / P0; indices: edge or
+    cell ids), one linear solve each.  Returns (values, statuses) as numpy
+    arrays."""
+    Xstar = _dev_f64(Xstar, (t.V, 2))
+    dCdX = _dev_f64(dCdX, (t.V, 2))
+    prm, keep = make_params(params, t.n, t.E)
+    k = np.ascontiguousarray(kinds, dtype=np.int32)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    out = np.zeros(k.size, dtype=np.float64)
+    st = np.zeros(k.size, dtype=np.int32)
+    capi.check(capi.vx_sensitivity_grad(t.handle, _ptr(Xstar), C.byref(prm), _ptr(dCdX), k.size,
+                                        k.ctypes.data, ix.ctypes.data, solver, rtol, max_iter,
+                                        out.ctypes.data, st.ctypes.data, _stream()),
+               "vx_sensitivity_grad")
+    return out, st
+
+
 def _make_equilibrium_fn():
     torch = _torch()
 
@@ -553,6 +574,51 @@ def vx_equilibrium_grad_batched(b: Batch, Xstar, params, dCdX, cg_rtol=1e-10, cg
         capi.check(st, "vx_equilibrium_grad_batched")
     return g, [GradResult(x.status, x.cg_iters, x.cg_rel_residual, x.cost, tuple(x.nudged_iters))
                for x in r]
+
+
+def vx_batch_grad(b: Batch, X, params, cost, cost_data, what=3, free=None, mode=VX_EP_CENTERED,
+                  beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, inner=None, ep_f64=0):
+    """The batched gradient workload in one launch (see vx.h): relax every
+    tissue (X: device f64 [sum V, 2], updated in place to X*), then the
+    adjoint (what & 1) and / or EP (what & 2) gradients of the built-in
+    cost.  Returns (adjoint dict, EP dict of device f64 tensors lam / A0 /
+    P0, list of (MinResult, adjoint GradResult, EP GradResult))."""
+    torch = _torch()
+    if not (hasattr(X, "is_cuda") and X.is_cuda and X.dtype == torch.float64
+            and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (updated in place)")
+    Vt, Et, nt = int(b.V.sum()), int(b.E.sum()), int(b.n.sum())
+    prm, keep = make_batch_params(params, b)
+    fo = min_opts(**(free or {}))
+    go = capi.vx_grad_opts()
+    capi.vx_grad_opts_default(C.byref(go))
+    go.mode, go.beta, go.cg_rtol, go.cg_max_iter, go.cost = mode, beta, cg_rtol, cg_max_iter, cost
+    go.ep_f64 = ep_f64
+    cd = _dev_f64(cost_data)
+    go.cost_data = cd.data_ptr()
+    if inner is not None:
+        go.inner = min_opts(**inner)
+    mk = lambda: {k: torch.empty(m, dtype=torch.float64, device="cuda")
+                  for k, m in (("lam", Et), ("A0", nt), ("P0", nt))}
+    ga = mk() if what & capi.VX_GRAD_ADJOINT else {}
+    ge = mk() if what & capi.VX_GRAD_EP else {}
+    r = (capi.vx_batch_grad_result * b.count)()
+    st = capi.vx_batch_grad(b.handle, _ptr(X), C.byref(prm), C.byref(fo), C.byref(go), what,
+                            _ptr(ga.get("lam")), _ptr(ga.get("A0")), _ptr(ga.get("P0")),
+                            _ptr(ge.get("lam")), _ptr(ge.get("A0")), _ptr(ge.get("P0")), r,
+                            _stream())
+    if st not in (capi.VX_OK, capi.VX_ERR_INDEFINITE):
+        capi.check(st, "vx_batch_grad")
+    out = []
+    for x in r:
+        f = x.free
+        out.append((MinResult(f.status, f.iters, f.n_t1, f.n_stretch, f.n_short_edges,
+                              f.n_inverted, f.fmax, f.energy, f.path_used, f.force_evals),
+                    GradResult(x.adjoint.status, x.adjoint.cg_iters, x.adjoint.cg_rel_residual,
+                               x.adjoint.cost, tuple(x.adjoint.nudged_iters)),
+                    GradResult(x.ep.status, x.ep.cg_iters, x.ep.cg_rel_residual, x.ep.cost,
+                               tuple(x.ep.nudged_iters))))
+    return ga, ge, out
 
 
 def vx_grid_barrier_selftest(ctas, absent_rank=-1, rounds=8, wait_s=0.25):

@@ -23,7 +23,8 @@ VX_OK, VX_NOT_CONVERGED, VX_ERR_INVALID_ARG, VX_ERR_DEGENERATE_SEEDS, VX_ERR_CUD
     VX_ERR_INDEFINITE, VX_ERR_TIMEOUT, VX_ERR_NONFINITE, VX_ERR_TOPOLOGY = range(10)
 VX_F64, VX_F32 = 0, 1
 VX_FIRE, VX_GD = 0, 1
-VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD = 0, 1, 2
+VX_ADJOINT_CG, VX_EP_CENTERED, VX_EP_FORWARD, VX_ADJOINT_MINRES = 0, 1, 2, 3
+VX_PARAM_LAMBDA, VX_PARAM_A0, VX_PARAM_P0 = 0, 1, 2
 VX_COST_NONE, VX_COST_V2V, VX_COST_ANISO = 0, 1, 2
 VX_PATH_AUTO, VX_PATH_RESIDENT, VX_PATH_PLAIN, VX_PATH_CLUSTER, VX_PATH_GRID = 0, 1, 2, 3, 4
 
@@ -119,6 +120,9 @@ vx_energy_forces_noalloc = _sig("vx_energy_forces_noalloc", C.c_int, C.c_void_p,
                                 C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p,
                                 C.POINTER(vx_params), C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p)
+vx_sensitivity_grad = _sig("vx_sensitivity_grad", C.c_int, C.c_void_p, C.c_void_p,
+                           C.POINTER(vx_params), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                           C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p)
 vx_minimize_async = _sig("vx_minimize_async", C.c_int, C.c_void_p, C.c_void_p,
                          C.POINTER(vx_params), C.POINTER(vx_min_opts), C.c_void_p, C.c_void_p)
 vx_equilibrium_grad_async = _sig("vx_equilibrium_grad_async", C.c_int, C.c_void_p, C.c_void_p,
@@ -143,6 +147,15 @@ vx_batch_autotune = _sig("vx_batch_autotune", C.c_int, C.c_void_p, C.c_void_p,
 vx_equilibrium_grad_batched = _sig("vx_equilibrium_grad_batched", C.c_int, C.c_void_p, C.c_void_p,
                                    C.POINTER(vx_batch_params), C.c_void_p, C.c_double, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+class vx_batch_grad_result(C.Structure):
+    _fields_ = [("free", vx_min_result), ("adjoint", vx_grad_result), ("ep", vx_grad_result)]
+
+
+VX_GRAD_ADJOINT, VX_GRAD_EP = 1, 2
+vx_batch_grad = _sig("vx_batch_grad", C.c_int, C.c_void_p, C.c_void_p, C.POINTER(vx_batch_params),
+                     C.POINTER(vx_min_opts), C.POINTER(vx_grad_opts), C.c_int32, C.c_void_p,
+                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                     C.c_void_p)
 vx_batch_aniso_cost = _sig("vx_batch_aniso_cost", C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -153,7 +166,8 @@ EXPORTED = ["vx_last_error", "vx_version", "vx_build_mesh", "vx_seed_order", "vx
             "vx_equilibrium_grad",
             "vx_batch_create", "vx_batch_destroy", "vx_batch_restore", "vx_batch_sizes",
             "vx_batch_topology", "vx_energy_forces_noalloc", "vx_grid_barrier_selftest",
-            "vx_minimize_async", "vx_equilibrium_grad_async",
+            "vx_minimize_async", "vx_equilibrium_grad_async", "vx_batch_grad",
+            "vx_sensitivity_grad",
             "vx_minimize_batched", "vx_batch_autotune", "vx_equilibrium_grad_batched",
             "vx_batch_aniso_cost"]
 

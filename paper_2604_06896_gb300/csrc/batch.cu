@@ -62,6 +62,12 @@ struct vx_batch_s {
   double* Xtune;
   // image shifts of the exit-time wrap [V_tot]
   int2* wrapk;
+  // batched gradient workload: nudged equilibria, grad_X C at X*,
+  // per-tissue anisotropy scratch, results; its own graph cache
+  double *gXp, *gXm, *gdC, *gaws;
+  void* gout;
+  cudaGraphExec_t gexec2;
+  std::vector<unsigned char> gkey2;
 };
 
 namespace vx {
@@ -266,6 +272,199 @@ __global__ void __launch_bounds__(T) k_adj_batch(BatchAdjArgs g) {
                        g.X + 2 * (size_t)d.vbase, g.g_lam ? g.g_lam + d.ebase : nullptr,
                        g.g_A0 ? g.g_A0 + d.cbase : nullptr, g.g_P0 ? g.g_P0 + d.cbase : nullptr,
                        g.out + g.order[k]);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------- batched gradient workload
+
+// Per tissue: the free relaxation, the adjoint and the two EP phases.
+struct BatchGradOut {
+  MinOut free, plus, minus;
+  AdjOut adj;
+  double cost;
+};
+
+struct BatchGradArgs {
+  BatchArgs b;              // topology, workspaces, parameters, free options
+  MinParams nud;            // nudged-phase options (cost, q_target / X_target)
+  int do_adjoint, do_ep, centered, ep_f64;
+  double beta, rtol;
+  int cg_max_iter;
+  double *Xp, *Xm, *dC, *aws;  // [V][2], [V][2], [V][2], per tissue 3 n
+  void *cell4, *ax, *ar, *ap, *az, *apre;
+  double *ga_lam, *ga_A0, *ga_P0, *ge_lam, *ge_A0, *ge_P0;
+  BatchGradOut* out;
+};
+
+template <class P>
+__device__ __forceinline__ View<P> batch_view(const BatchArgs& g, const BatchDesc& d, void* X) {
+  View<P> v;
+  v.vnb = nullptr;
+  v.vfc = nullptr;
+  v.ccnt = nullptr;
+  v.ccor = nullptr;
+  v.cedge = nullptr;
+  v.n = d.n;
+  v.V = d.V;
+  v.E = d.E;
+  v.box = P::make_box(d.Lx, d.Ly);
+  v.Lx = d.Lx;
+  v.Ly = d.Ly;
+  v.X = (typename P::Pos*)X;
+  v.tgt = g.tgt + d.hbase;
+  v.nxt = g.nxt + d.hbase;
+  v.face = g.face + d.hbase;
+  v.vout = g.vout + 3 * d.vbase;
+  v.ffirst = g.ffirst + d.cbase;
+  return v;
+}
+
+__device__ __forceinline__ ParamsD batch_params(const BatchArgs& g, const BatchDesc& d) {
+  ParamsD prm;
+  prm.KA = g.KA ? g.KA + d.cbase : nullptr;
+  prm.KP = g.KP ? g.KP + d.cbase : nullptr;
+  prm.A0 = g.A0 ? g.A0 + d.cbase : nullptr;
+  prm.P0 = g.P0 ? g.P0 + d.cbase : nullptr;
+  prm.lam = g.lam ? g.lam + d.ebase : nullptr;
+  prm.KA_s = d.KA;
+  prm.KP_s = d.KP;
+  prm.A0_s = d.A0;
+  prm.P0_s = d.P0;
+  prm.lam_s = d.lam;
+  return prm;
+}
+
+// One nudged phase from X* (positions in `Xs`) into Xout, in precision Q.
+template <class Q, int T>
+__device__ void batch_nudged(const BatchGradArgs& a, const BatchDesc& d, const ParamsD& prm,
+                             MinParams mp, double s, const double* Xs, double* Xout, Slots sl,
+                             MinOut* out) {
+  using R2 = typename Vec2Of<typename Q::R>::T;
+  const BatchArgs& g = a.b;
+  View<Q> v = batch_view<Q>(g, d, (typename Q::Pos*)g.Xw + d.vbase);
+  mp.nudge_s = s;
+  min_body_mem<Q, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+                     prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, mp, Xs, Xout,
+                     out);
+  __syncthreads();
+}
+
+template <class P, int T>
+__global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
+  using R = typename P::R;
+  using R2 = typename Vec2Of<R>::T;
+  using R4 = typename Vec2Of<R>::T4;
+  __shared__ int item;
+  __shared__ double slots[3][4 * (T / 32 + 1)];
+  __shared__ double Gs[3];
+  const BatchArgs& g = a.b;
+  BlockTeam<T> tm;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) item = atomicAdd(g.counter, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= g.count) break;
+    const int tk = g.order[k];
+    const BatchDesc d = g.desc[tk];
+    const ParamsD prm = batch_params(g, d);
+    BatchGradOut* o = a.out + tk;
+    Slots sl = {slots[0], slots[1], slots[2]};
+    double* Xk = (double*)g.X + 2 * (size_t)d.vbase;
+    // 1. the free equilibrium X* (T1 on, per the free options)
+    {
+      View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
+      min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+                         prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xk, Xk,
+                         &o->free);
+      __syncthreads();
+    }
+    // 2. the outer cost and grad_X C at X* (FP64, on the returned positions)
+    View<PolF64> vs = batch_view<PolF64>(g, d, Xk);
+    double2* dC = (double2*)a.dC + d.vbase;
+    // per tissue 4 n doubles (even offsets: the centroids are double2)
+    double2* acent = (double2*)(a.aws + 4 * (size_t)d.cbase);
+    int* akk = (int*)(a.aws + 4 * (size_t)d.cbase + 2 * (size_t)d.n);
+    MinParams mpn = a.nud;
+    if (mpn.cost == 1) mpn.cost_data = a.nud.cost_data + 2 * (size_t)d.vbase;  // X_target slice
+    mpn.aniso_ws = mpn.cost == 2 ? (double*)acent : nullptr;
+    double cost = 0.0;
+    if (mpn.cost == 1) {
+      double s1[1] = {0};
+      for (int i = tid; i < d.V; i += T) {
+        double gx, gy;
+        v2v_grad(vs, i, mpn.cost_data, gx, gy);
+        dC[i] = make_double2(gx, gy);
+        s1[0] += 0.5 * d.V * (gx * gx + gy * gy);
+      }
+      tm.template reduce<1>(s1, sl.a, 0);
+      cost = s1[0];
+    } else {
+      double Q[3] = {0, 0, 0};
+      for (int c = tid; c < d.n; c += T) {
+        double sxx, syy, sxy;
+        cell_shape(vs, c, acent, akk, sxx, syy, sxy);
+        Q[0] += sxx;
+        Q[1] += syy;
+        Q[2] += sxy;
+      }
+      tm.template reduce<3>(Q, sl.a, 0);
+      for (int q = 0; q < 3; ++q) Q[q] /= d.n;
+      double G[3];
+      aniso_dC_dQ(Q, mpn.cost_data, G);
+      const double T_ = Q[0] + Q[1];
+      const double q1 = (Q[0] - Q[1]) / T_ - mpn.cost_data[0];
+      const double q2 = 2.0 * Q[2] / T_ - mpn.cost_data[1];
+      cost = q1 * q1 + q2 * q2;
+      for (int i = tid; i < d.V; i += T) {
+        double gx, gy;
+        aniso_grad_vertex(vs, i, acent, akk, G, gx, gy);
+        dC[i] = make_double2(gx, gy);
+      }
+    }
+    if (tid == 0) o->cost = cost;
+    __syncthreads();
+    // 3. the adjoint: H lam = Pi grad_X C by preconditioned CG, g = -(d2E/dX dth)^T lam
+    if (a.do_adjoint) {
+      View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
+      adj_body_mem<P, T>(v, (R4*)a.cell4 + d.cbase, (R2*)a.ax + d.vbase, (R2*)a.ar + d.vbase,
+                         (R2*)a.ap + d.vbase, (R2*)a.az + d.vbase, (R4*)a.apre + d.vbase, prm.lam,
+                         sl, prm, (const double*)dC, a.rtol, a.cg_max_iter, Xk,
+                         a.ga_lam ? a.ga_lam + d.ebase : nullptr,
+                         a.ga_A0 ? a.ga_A0 + d.cbase : nullptr,
+                         a.ga_P0 ? a.ga_P0 + d.cbase : nullptr, &o->adj);
+      __syncthreads();
+    }
+    // 4. equilibrium propagation: E +/- (beta/2) C from X*, then the
+    //    difference of d_theta E over beta
+    if (a.do_ep) {
+      double* Xp = a.Xp + 2 * (size_t)d.vbase;
+      double* Xm = a.Xm + 2 * (size_t)d.vbase;
+      const double sp = a.centered ? 0.5 * a.beta : a.beta;
+      if (a.ep_f64) {
+        batch_nudged<PolF64, T>(a, d, prm, mpn, sp, Xk, Xp, sl, &o->plus);
+        if (a.centered) batch_nudged<PolF64, T>(a, d, prm, mpn, -sp, Xk, Xm, sl, &o->minus);
+      } else {
+        batch_nudged<P, T>(a, d, prm, mpn, sp, Xk, Xp, sl, &o->plus);
+        if (a.centered) batch_nudged<P, T>(a, d, prm, mpn, -sp, Xk, Xm, sl, &o->minus);
+      }
+      View<PolF64> vp = batch_view<PolF64>(g, d, Xp);
+      View<PolF64> vm = batch_view<PolF64>(g, d, a.centered ? Xm : Xk);
+      if (a.ge_lam)
+        for (int e = tid; e < d.E; e += T)
+          a.ge_lam[d.ebase + e] = (edge_len_d(vp, 2 * e) - edge_len_d(vm, 2 * e)) / a.beta;
+      if (a.ge_A0 || a.ge_P0)
+        for (int c = tid; c < d.n; c += T) {
+          double Ap, Pp, Am, Pm;
+          cell_geometry(vp, c, Ap, Pp, 0.0, nullptr);
+          cell_geometry(vm, c, Am, Pm, 0.0, nullptr);
+          if (a.ge_A0) a.ge_A0[d.cbase + c] = -2.0 * prm.ka(c) * (Ap - Am) / a.beta;
+          if (a.ge_P0) a.ge_P0[d.cbase + c] = -2.0 * prm.kp(c) * (Pp - Pm) / a.beta;
+        }
+    }
+    (void)Gs;
     __syncthreads();
   }
 }
@@ -563,6 +762,11 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   A((void**)&b->d_adj_out, sizeof(vx::AdjOut) * count);
   A((void**)&b->aniso_ws, 8 * (3 * (size_t)nb + (size_t)count + 8));
   A((void**)&b->Xtune, 16 * (size_t)vb);
+  A((void**)&b->gXp, 16 * (size_t)vb);
+  A((void**)&b->gXm, 16 * (size_t)vb);
+  A((void**)&b->gdC, 16 * (size_t)vb);
+  A((void**)&b->gaws, 8 * 4 * (size_t)nb);
+  A(&b->gout, sizeof(vx::BatchGradOut) * count);
   if (e != cudaSuccess) {
     vx_batch_destroy(b);
     return fail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA,
@@ -594,7 +798,9 @@ vx_status vx_batch_destroy(vx_batch b) {
   void* ptrs[] = {b->d_desc, b->d_order, b->d_counter, b->tgt,  b->nxt,   b->face,  b->vout,
                   b->ffirst, b->tgt0,    b->nxt0,      b->face0, b->vout0, b->ffirst0, b->Xw,
                   b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out,
-                  b->adj_ws, b->d_adj_out, b->wrapk, b->aniso_ws, b->Xtune};
+                  b->adj_ws, b->d_adj_out, b->wrapk, b->aniso_ws, b->Xtune, b->gXp, b->gXm,
+                  b->gdC, b->gaws, b->gout};
+  if (b->gexec2) cudaGraphExecDestroy(b->gexec2);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -974,3 +1180,189 @@ vx_status vx_batch_aniso_cost(vx_batch b, const double* X, const double* q_targe
 }
 
 }  // extern "C"
+
+namespace {
+
+vx::MinParams min_params_of(const vx_min_opts* o) {
+  vx::MinParams mp = {};
+  mp.method = o->method;
+  mp.tol = o->tol;
+  mp.patience = o->patience;
+  mp.max_iter = o->max_iter;
+  mp.gd_lr = o->gd_lr;
+  mp.dt0 = o->dt0;
+  mp.dt_max = o->dt_max;
+  mp.n_min = o->n_min;
+  mp.f_inc = o->f_inc;
+  mp.f_dec = o->f_dec;
+  mp.alpha0 = o->alpha0;
+  mp.f_alpha = o->f_alpha;
+  mp.l_min = o->l_min;
+  mp.wrap = o->wrap ? 1 : 0;
+  return mp;
+}
+
+template <class K>
+int grad_grid(K kernel, int count) {
+  int occ = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess) return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(count, occ * sms));
+}
+
+}  // namespace
+
+extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params* p,
+                                   const vx_min_opts* fo, const vx_grad_opts* go, int32_t what,
+                                   double* ga_lambda, double* ga_A0, double* ga_P0,
+                                   double* ge_lambda, double* ge_A0, double* ge_P0,
+                                   vx_batch_grad_result* r, void* stream) {
+  if (!b || !X || !p || !fo || !go || !r) return fail(VX_ERR_INVALID_ARG, "NULL argument");
+  if (!(what & (VX_GRAD_ADJOINT | VX_GRAD_EP)) || (what & ~(VX_GRAD_ADJOINT | VX_GRAD_EP)))
+    return fail(VX_ERR_INVALID_ARG, "what must be VX_GRAD_ADJOINT, VX_GRAD_EP or both");
+  if (go->cost != VX_COST_V2V && go->cost != VX_COST_ANISO)
+    return fail(VX_ERR_INVALID_ARG, "the batched gradient needs a built-in cost (v2v or anisotropy)");
+  if (!go->cost_data) return fail(VX_ERR_INVALID_ARG, "cost_data is NULL");
+  if ((what & VX_GRAD_EP) && go->mode != VX_EP_CENTERED && go->mode != VX_EP_FORWARD)
+    return fail(VX_ERR_INVALID_ARG, "EP needs go->mode VX_EP_CENTERED or VX_EP_FORWARD");
+  if ((what & VX_GRAD_EP) && !(go->beta > 0)) return fail(VX_ERR_INVALID_ARG, "beta must be positive");
+  if (fo->method != VX_FIRE && fo->method != VX_GD) return fail(VX_ERR_INVALID_ARG, "method");
+  if (fo->max_iter < 0 || fo->patience < 1 || !(fo->dt0 > 0) || !(fo->dt_max > 0) ||
+      go->inner.max_iter < 0 || go->inner.patience < 1 || !(go->inner.dt0 > 0) ||
+      !(go->inner.dt_max > 0) || !(go->cg_rtol >= 0) || go->cg_max_iter < 0)
+    return fail(VX_ERR_INVALID_ARG, "invalid minimiser or CG options");
+  cudaStream_t s = (cudaStream_t)stream;
+  set_tissue_params(b, p);
+  if (cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(BatchDesc) * b->count,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(VX_ERR_CUDA, "descriptor upload");
+  vx::BatchGradArgs a = {};
+  a.b = make_batch_args(b, X, p, min_params_of(fo));
+  a.b.mp.edge_events = nullptr;
+  a.nud = min_params_of(&go->inner);
+  a.nud.l_min = 0.0;   // fixed topology in the nudged phases
+  a.nud.wrap = 0;
+  a.nud.cost = go->cost;
+  a.nud.cost_data = go->cost_data;
+  a.do_adjoint = (what & VX_GRAD_ADJOINT) ? 1 : 0;
+  a.do_ep = (what & VX_GRAD_EP) ? 1 : 0;
+  a.centered = go->mode == VX_EP_CENTERED ? 1 : 0;
+  a.ep_f64 = go->ep_f64 ? 1 : 0;
+  a.beta = go->beta;
+  a.rtol = go->cg_rtol;
+  a.cg_max_iter = go->cg_max_iter;
+  a.Xp = b->gXp;
+  a.Xm = b->gXm;
+  a.dC = b->gdC;
+  a.aws = b->gaws;
+  const AdjLayout L = adj_layout(b->dtype, b->n_tot, b->V_tot);
+  unsigned char* w = (unsigned char*)b->adj_ws;
+  a.cell4 = w;
+  a.ax = w + L.o_x;
+  a.ar = w + L.o_x + L.vec;
+  a.ap = w + L.o_x + 2 * L.vec;
+  a.az = w + L.o_x + 3 * L.vec;
+  a.apre = w + L.o_pre;
+  a.ga_lam = ga_lambda;
+  a.ga_A0 = ga_A0;
+  a.ga_P0 = ga_P0;
+  a.ge_lam = ge_lambda;
+  a.ge_A0 = ge_A0;
+  a.ge_P0 = ge_P0;
+  a.out = (vx::BatchGradOut*)b->gout;
+  const bool f64 = b->dtype == VX_F64;
+  const int grid = f64 ? grad_grid(vx::k_grad_batch<vx::PolF64, 256>, b->count)
+                       : grad_grid(vx::k_grad_batch<vx::PolF32, 256>, b->count);
+  if (grid < 1) return fail(VX_ERR_CUDA, "batched gradient kernel cannot be resident");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4, st);
+    // the wrap reports into the forward results' wrap_err slots
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_out, 0, sizeof(vx::MinOut) * b->count, st);
+    if (e != cudaSuccess) return e;
+    if (f64)
+      vx::k_grad_batch<vx::PolF64, 256><<<grid, 256, 0, st>>>(a);
+    else
+      vx::k_grad_batch<vx::PolF32, 256><<<grid, 256, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !a.b.mp.wrap) return e;
+    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, st>>>(b->d_desc, b->count, X, b->tgt,
+                                                               b->wrapk, b->d_out);
+    return cudaGetLastError();
+  };
+  // Replay the captured launch when the arguments are unchanged.
+  std::vector<unsigned char> key(sizeof(a) + sizeof(int));
+  std::memcpy(key.data(), &a, sizeof(a));
+  std::memcpy(key.data() + sizeof(a), &grid, sizeof(int));
+  cudaError_t e = cudaSuccess;
+  if (!b->gexec2 || !same_key(b->gkey2, key.data(), key.size())) {
+    if (b->gexec2) cudaGraphExecDestroy(b->gexec2);
+    b->gexec2 = nullptr;
+    cudaStream_t cs;
+    cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    cudaGraph_t gr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e2 = enqueue(cs);
+      e = cudaStreamEndCapture(cs, &gr);
+      if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&b->gexec2, gr, 0);
+        cudaGraphDestroy(gr);
+      }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    b->gkey2 = key;
+  }
+  e = cudaGraphLaunch(b->gexec2, s);
+  std::vector<vx::BatchGradOut> out(b->count);
+  std::vector<vx::MinOut> wout(b->count);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out.data(), b->gout, sizeof(vx::BatchGradOut) * b->count,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && a.b.mp.wrap)
+    e = cudaMemcpyAsync(wout.data(), b->d_out, sizeof(vx::MinOut) * b->count,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("vx_batch_grad: ") + cudaGetErrorString(e));
+  vx_status worst = VX_OK;
+  for (int k = 0; k < b->count; ++k) {
+    const vx::BatchGradOut& o = out[k];
+    vx_min_result& f = r[k].free;
+    f.status = (a.b.mp.wrap && wout[k].wrap_err) ? (int)VX_ERR_TOPOLOGY : o.free.status;
+    f.iters = o.free.iters;
+    f.n_t1 = o.free.n_t1;
+    f.n_stretch = o.free.n_stretch;
+    f.n_short_edges = o.free.n_short;
+    f.n_inverted = o.free.n_inverted;
+    f.fmax = o.free.fmax;
+    f.energy = o.free.energy;
+    f.path_used = VX_PATH_RESIDENT;
+    f.force_evals = o.free.force_evals;
+    vx_grad_result& ga = r[k].adjoint;
+    ga.status = a.do_adjoint ? o.adj.status : VX_OK;
+    ga.cg_iters = a.do_adjoint ? o.adj.iters : 0;
+    ga.cg_rel_residual = a.do_adjoint ? o.adj.rel_residual : 0.0;
+    ga.cost = o.cost;
+    ga.nudged_iters[0] = ga.nudged_iters[1] = 0;
+    vx_grad_result& ge = r[k].ep;
+    ge.status = !a.do_ep ? VX_OK
+                         : ((o.plus.status == VX_OK && (!a.centered || o.minus.status == VX_OK))
+                                ? VX_OK
+                                : VX_NOT_CONVERGED);
+    ge.cg_iters = 0;
+    ge.cg_rel_residual = 0.0;
+    ge.cost = o.cost;
+    ge.nudged_iters[0] = a.do_ep ? o.plus.iters : 0;
+    ge.nudged_iters[1] = (a.do_ep && a.centered) ? o.minus.iters : 0;
+    if (ga.status == VX_ERR_INDEFINITE) worst = VX_ERR_INDEFINITE;
+    if (f.status == VX_ERR_NONFINITE || f.status == VX_ERR_TOPOLOGY) worst = (vx_status)f.status;
+  }
+  if (worst == VX_ERR_INDEFINITE)
+    set_error("CG met a direction of non-positive curvature in at least one tissue");
+  return worst;
+}

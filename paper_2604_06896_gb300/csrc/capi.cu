@@ -528,16 +528,16 @@ __global__ void k_min_result(const vx::MinOut* o, int path, vx_min_result* r) {
 
 std::string grad_opts_error(const double* dCdX, const vx_grad_opts* o) {
   std::string m;
-  if (o->mode != VX_ADJOINT_CG && o->mode != VX_EP_CENTERED && o->mode != VX_EP_FORWARD)
+  if (o->mode != VX_ADJOINT_CG && o->mode != VX_EP_CENTERED && o->mode != VX_EP_FORWARD &&
+      o->mode != VX_ADJOINT_MINRES)
     return "unknown gradient mode";
-  if (o->mode == VX_ADJOINT_CG && !dCdX && o->cost == VX_COST_NONE)
-    return "adjoint needs dCdX or a built-in cost";
-  if (o->mode != VX_ADJOINT_CG && o->cost == VX_COST_NONE)
-    return "equilibrium propagation needs a built-in cost";
+  const bool ep = o->mode == VX_EP_CENTERED || o->mode == VX_EP_FORWARD;
+  if (!ep && !dCdX && o->cost == VX_COST_NONE) return "adjoint needs dCdX or a built-in cost";
+  if (ep && o->cost == VX_COST_NONE) return "equilibrium propagation needs a built-in cost";
   if (o->cost != VX_COST_NONE && o->cost != VX_COST_V2V && o->cost != VX_COST_ANISO)
     return "unknown cost";
   if (o->cost != VX_COST_NONE && !o->cost_data) return "cost_data is NULL";
-  if (o->mode != VX_ADJOINT_CG && !(o->beta > 0)) return "beta must be positive";
+  if (ep && !(o->beta > 0)) return "beta must be positive";
   if (!min_opts_ok(&o->inner, &m)) return m;
   return "";
 }
@@ -565,6 +565,27 @@ vx_status vx_minimize_async(vx_tissue t, double* X, const vx_params* p, const vx
     return VX_ERR_CUDA;
   }
   return VX_OK;
+}
+
+vx_status vx_sensitivity_grad(vx_tissue t, const double* Xstar, const vx_params* p,
+                              const double* dCdX, int32_t count, const int32_t* kind,
+                              const int32_t* index, int32_t solver, double rtol, int32_t max_iter,
+                              double* out, int32_t* status, void* stream) {
+  if (!t || !Xstar || !dCdX || !kind || !index || !out) return invalid("NULL argument");
+  if (count < 0) return invalid("count must be >= 0");
+  std::string m;
+  if (!params_ok(p, &m)) return invalid(m);
+  if (solver != VX_ADJOINT_CG && solver != VX_ADJOINT_MINRES)
+    return invalid("solver must be VX_ADJOINT_CG or VX_ADJOINT_MINRES");
+  if (!(rtol >= 0) || max_iter < 0) return invalid("invalid solver options");
+  for (int k = 0; k < count; ++k) {
+    const int lim = kind[k] == VX_PARAM_LAMBDA ? t->E : t->n;
+    if (kind[k] < VX_PARAM_LAMBDA || kind[k] > VX_PARAM_P0) return invalid("unknown parameter kind");
+    if (index[k] < 0 || index[k] >= lim) return invalid("parameter index out of range");
+  }
+  return vx::sensitivity(t, Xstar, to_params(p), dCdX, count, kind, index,
+                         solver == VX_ADJOINT_MINRES, rtol, max_iter, 50, out, status,
+                         as_stream(stream));
 }
 
 vx_status vx_equilibrium_grad_async(vx_tissue t, const double* Xstar, const vx_params* p,

@@ -31,6 +31,8 @@ __global__ void k_aniso_grad(View<PolF64> v, const double2* cent, const int* kk,
                              double2* out);
 vx_status adjoint_plain(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
                         int check_every, AdjOut* out, cudaStream_t s);
+vx_status adjoint_minres(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
+                         const AdjParams& ap, int check_every, AdjOut* out, cudaStream_t s);
 // defined in persistent.cu
 vx_status adjoint_solve(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
                         int path, AdjOut* out_host, AdjOut* out_dev, cudaStream_t s);
@@ -96,7 +98,7 @@ __global__ void k_grad_result(const GradDev* g, int mode, int centered, int cost
                               vx_grad_result* r) {
   if (threadIdx.x || blockIdx.x) return;
   vx_grad_result o;
-  if (mode == VX_ADJOINT_CG) {
+  if (mode == VX_ADJOINT_CG || mode == VX_ADJOINT_MINRES) {
     o.status = g->adj.status;
     o.cg_iters = g->adj.iters;
     o.cg_rel_residual = g->adj.rel_residual;
@@ -160,7 +162,8 @@ vx_status equilibrium_grad_impl(vx_tissue_s* t, const double* Xstar, const Param
                                 vx_grad_result* r_dev, cudaStream_t s) {
   const bool async = r_dev != nullptr;
   GradDev* gd = grad_dev(t);
-  if (o->mode == VX_ADJOINT_CG) {
+  if (o->mode == VX_ADJOINT_CG || o->mode == VX_ADJOINT_MINRES) {
+    const bool minres = o->mode == VX_ADJOINT_MINRES;
     const double* rhs = dCdX;
     const bool aniso = !dCdX && o->cost == VX_COST_ANISO;
     if (aniso) {
@@ -179,19 +182,20 @@ vx_status equilibrium_grad_impl(vx_tissue_s* t, const double* Xstar, const Param
     ap.g_P0 = g_P0;
     AdjOut out = {};
     vx_status st;
-    if (o->inner.path == VX_PATH_PLAIN) {
+    if (o->inner.path == VX_PATH_PLAIN || minres) {
       // one launch per sub-step, status polled by the host
       if (async) {
-        set_error("the plain adjoint path polls the host and cannot run asynchronously");
+        set_error("the plain adjoint path and MINRES poll the host and cannot run asynchronously");
         return VX_ERR_INVALID_ARG;
       }
-      st = adjoint_plain(t, Xstar, prm, ap, o->inner.check_every, &out, s);
+      st = minres ? adjoint_minres(t, Xstar, prm, ap, o->inner.check_every, &out, s)
+                  : adjoint_plain(t, Xstar, prm, ap, o->inner.check_every, &out, s);
     } else {
       st = adjoint_solve(t, Xstar, prm, ap, o->inner.path, async ? nullptr : &out, &gd->adj, s);
     }
     if (st != VX_OK) return st;
     if (async) {
-      k_grad_result<<<1, 1, 0, s>>>(gd, VX_ADJOINT_CG, 0, aniso ? 0 : 1, r_dev);
+      k_grad_result<<<1, 1, 0, s>>>(gd, o->mode, 0, aniso ? 0 : 1, r_dev);
       return cudaGetLastError() == cudaSuccess ? VX_OK : VX_ERR_CUDA;
     }
     double c = 0.0;

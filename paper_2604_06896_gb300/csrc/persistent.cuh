@@ -853,6 +853,27 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
   for (int w = tid; w < (E + 31) / 32; w += T) shortbits[w] = 0;
   for (int w = tid; w < (V + 31) / 32; w += T) touched[w] = 0;
   tm.sync();
+  // Nudged phase of equilibrium propagation: -s Pi grad_X C (v2v: the mean
+  // of grad C taken once, the centroid being conserved; anisotropy: the
+  // gradient sums to zero by itself).
+  const bool nudged_v2v = mp.cost == 1 && mp.nudge_s != 0.0;
+  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr;
+  double2* acent = nudged_aniso ? (double2*)mp.aniso_ws : nullptr;
+  int* akk = nudged_aniso ? (int*)(mp.aniso_ws + 2 * (size_t)n) : nullptr;
+  double nmx = 0, nmy = 0;
+  if (nudged_v2v) {
+    double s2[2] = {0, 0};
+    for (int i = tid; i < V; i += T) {
+      double gx, gy;
+      v2v_grad(vw, i, mp.cost_data, gx, gy);
+      s2[0] += gx;
+      s2[1] += gy;
+    }
+    tm.template reduce<2>(s2, sl.c, 0);
+    nmx = s2[0] / V;
+    nmy = s2[1] / V;
+    tm.sync();
+  }
   const R lminR = (R)mp.l_min;
   double dt = mp.dt0, alpha = mp.alpha0, fmx = 0;
   int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
@@ -898,10 +919,40 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     } else {
       __syncthreads();
     }
+    // Nudged phases (no T1, so bank c is free): anisotropy dC/dQ from the
+    // cells' shapes; the reduction's barrier publishes the centroids.
+    double G[3] = {0, 0, 0};
+    if (nudged_aniso) {
+      double Q[3] = {0, 0, 0};
+      for (int c = tid; c < n; c += T) {
+        double sxx, syy, sxy;
+        cell_shape(vw, c, acent, akk, sxx, syy, sxy);
+        Q[0] += sxx;
+        Q[1] += syy;
+        Q[2] += sxy;
+      }
+      tm.template reduce<3>(Q, sl.c, 0);
+      Q[0] /= n;
+      Q[1] /= n;
+      Q[2] /= n;
+      aniso_dC_dQ(Q, mp.cost_data, G);
+    }
     double red[4] = {0, 0, 0, 0};
     for (int i = tid; i < V; i += T) {
       R fx, fy;
       vertex_force(vw, i, cell, lam, prm.lam_s, fx, fy);
+      if (nudged_v2v) {
+        double gx, gy;
+        v2v_grad(vw, i, mp.cost_data, gx, gy);
+        fx -= (R)(mp.nudge_s * (gx - nmx));
+        fy -= (R)(mp.nudge_s * (gy - nmy));
+      }
+      if (nudged_aniso) {
+        double gx, gy;
+        aniso_grad_vertex(vw, i, acent, akk, G, gx, gy);
+        fx -= (R)(mp.nudge_s * gx);
+        fy -= (R)(mp.nudge_s * gy);
+      }
       R2 f;
       f.x = fx;
       f.y = fy;

@@ -54,12 +54,16 @@ namespace vx {
 //   ep:     the two nudged equilibria of equilibrium propagation, the cost
 //           and the two phases' results;
 //   aniso:  grad_X C of the anisotropy cost and its per-cell scratch.
+// Each region is a multiple of 32 doubles (256 bytes), so that every region
+// (and every [V][2] vector at an even offset inside it) is aligned for
+// double2 / double4 access.
+inline size_t work_r32(size_t x) { return (x + 31) & ~size_t(31); }
 inline size_t work_solver_doubles(int n, int V) {
-  return 12 * (size_t)V + 4 * (size_t)n + 3 * (size_t)((V + 255) / 256) + 128;
+  return work_r32(12 * (size_t)V + 4 * (size_t)n + 3 * (size_t)((V + 255) / 256) + 128);
 }
-inline size_t work_ep_doubles(int V) { return 4 * (size_t)V + 64; }
+inline size_t work_ep_doubles(int V) { return work_r32(4 * (size_t)V + 64); }
 inline size_t work_aniso_doubles(int n, int V) {
-  return 2 * (size_t)V + 3 * (size_t)n + 3 * (size_t)((n + 255) / 256) + 64;
+  return work_r32(2 * (size_t)V + 3 * (size_t)n + 3 * (size_t)((n + 255) / 256) + 64);
 }
 inline size_t work_total_doubles(int n, int V) {
   return work_solver_doubles(n, V) + work_ep_doubles(V) + work_aniso_doubles(n, V);
@@ -94,6 +98,10 @@ vx_status equilibrium_grad_impl(vx_tissue_s* t, const double* Xstar, const Param
                                 vx_grad_result* r_dev, cudaStream_t s);
 vx_status minimize_launch(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
                           int path, MinOut* out_dev, int* path_used, cudaStream_t s);
+vx_status sensitivity(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const double* dCdX,
+                      int count, const int32_t* kind, const int32_t* index, bool minres,
+                      double rtol, int max_iter, int check_every, double* out, int32_t* status,
+                      cudaStream_t s);
 size_t aniso_scratch_doubles(int n);
 vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double* gradX,
                           double* scratch, double* C, cudaStream_t s);

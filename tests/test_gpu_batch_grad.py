@@ -89,3 +89,115 @@ def test_batch_adjoint_matches_oracle(vx, relaxed, dtype, tol):
     if bb is not b:
         bb.close()
     torch.cuda.synchronize()
+
+
+def test_batch_grad_vs_oracle(vx):
+    """vx_batch_grad on four small FP64 tissues (anisotropy cost, per-cell
+    A0 and per-edge tensions as parameters): the free relaxation follows the
+    oracle's (same T1 decisions and topology), and the adjoint and centred
+    EP gradients of the one launch match the oracle's adjoint and EP at the
+    oracle's equilibrium."""
+    import torch
+    sizes, p0s = [60, 150, 90, 220], [3.5, 3.6, 3.55, 3.65]
+    cs = [vi.small_tissue(n, 620 + k, p0=p0, lam_range=(0.02, 0.1))
+          for k, (n, p0) in enumerate(zip(sizes, p0s))]
+    meshes = [omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"]) for c in cs]
+    rng = np.random.default_rng(621)
+    A0s = [rng.uniform(0.9, 1.1, n) for n in sizes]
+    b = vx.Batch(meshes, "f64")
+    X = torch.tensor(np.concatenate([m["vert"] for m in meshes]), dtype=torch.float64,
+                     device="cuda")
+    params = dict(KA=1.0, KP=1.0, A0=torch.tensor(np.concatenate(A0s), device="cuda"),
+                  P0=np.array(p0s), lam=torch.tensor(np.concatenate([c["lam"] for c in cs]),
+                                                     device="cuda"))
+    free = dict(tol=1e-11, max_iter=100000, dt0=0.01, dt_max=0.5, l_min=5e-3, wrap=0)
+    inner = dict(tol=1e-12, max_iter=100000, dt0=0.01, dt_max=0.5)
+    beta = 0.2
+    ga, ge, rs = vx.vx_batch_grad(b, X, params, vx.VX_COST_ANISO, QT, what=3, free=free,
+                                  beta=beta, cg_rtol=1e-13, inner=inner)
+    tops = b.topologies()
+    Xs = b.split(X.cpu().numpy())
+    for k in range(b.count):
+        p = dict(KA=1.0, KP=1.0, A0=A0s[k], P0=p0s[k], lam=cs[k]["lam"])
+        ro = osolv.relax(meshes[k]["vert"], meshes[k], p,
+                         osolv.MinOpts(tol=1e-11, max_iter=100000, dt0=0.01, dt_max=0.5),
+                         l_min=5e-3)
+        fr, ra, re = rs[k]
+        assert fr.converged and ro.converged
+        assert (fr.n_t1, fr.n_stretch) == (ro.n_t1, ro.n_stretch)
+        assert np.array_equal(tops[k]["he"], ro.tissue["he"])
+        assert np.abs(Xs[k] - ro.X).max() < 1e-7
+        t = ro.tissue
+        gradC = lambda Y: omodel.shape_tensor_anisotropy(Y, t, QT)[1]
+        C, G = omodel.shape_tensor_anisotropy(ro.X, t, QT)
+        g_adj, _, info = osolv.adjoint_grad(ro.X, t, p, G)
+        g_ep, _ = osolv.ep_grad(ro.X, t, p, gradC, beta, osolv.MinOpts(
+            tol=1e-12, max_iter=100000, dt0=0.01, dt_max=0.5), centered=True)
+        e0, e1 = b.ebase[k], b.ebase[k] + b.E[k]
+        c0, c1 = b.cbase[k], b.cbase[k] + b.n[k]
+        sl = {"lam": slice(e0, e1), "A0": slice(c0, c1), "P0": slice(c0, c1)}
+        ea = {q: rel(ga[q][sl[q]].cpu().numpy(), g_adj[q]) for q in ("lam", "A0")}
+        ee = {q: rel(ge[q][sl[q]].cpu().numpy(), g_ep[q]) for q in ("lam", "A0")}
+        print(f"batch grad tissue {k} n={sizes[k]}: free {fr.iters} it {fr.n_t1} T1; cg "
+              f"{ra.cg_iters}; EP {re.nudged_iters}; adjoint {ea}; EP {ee}")
+        assert ra.status == 0 and re.status == 0
+        assert abs(ra.cost - C) < 1e-9 * abs(C)
+        for q in ("lam", "A0"):
+            assert ea[q] < 1e-6, (k, q)
+            assert ee[q] < 1e-6, (k, q)
+    b.close()
+
+
+def test_batch_grad_c5_full_size(vx):
+    """The batched inverse-design workload at full size: 64 tissues of
+    10,000 cells, FP32, anisotropy cost, per-cell A0 and per-edge tensions,
+    free relaxation (T1 on, fixed budget), adjoint and centred EP (FP64
+    nudged phases) in one launch.  Checked on sampled tissues: the oracle's
+    energy and max |F| at the returned state agree with the GPU's; the
+    batched adjoint equals the single-tissue adjoint at the same state; EP
+    and the adjoint agree to the O(beta^2) and FP32 bounds."""
+    import torch
+    batch = vi.batch_c5()
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
+    b = vx.Batch(meshes, "f32")
+    X = torch.tensor(np.concatenate([m["vert"] for m in meshes]), dtype=torch.float64,
+                     device="cuda")
+    lam = torch.tensor(np.concatenate([c["lam"] for c in batch]), device="cuda")
+    A0 = torch.ones(int(b.n.sum()), dtype=torch.float64, device="cuda")
+    params = dict(KA=1.0, KP=1.0, A0=A0, P0=3.7, lam=lam)
+    free = dict(tol=1e-6, max_iter=10000, dt0=0.01, dt_max=0.5, l_min=5e-3)
+    inner = dict(tol=1e-7, max_iter=20000, dt0=0.01, dt_max=0.5)
+    ga, ge, rs = vx.vx_batch_grad(b, X, params, vx.VX_COST_ANISO, (0.1, 0.0), what=3, free=free,
+                                  beta=1e-2, cg_rtol=1e-6, inner=inner, ep_f64=1)
+    print("c5 free:", [r[0].status for r in rs].count(0), "converged of", b.count,
+          "; iters", min(r[0].iters for r in rs), max(r[0].iters for r in rs),
+          "; cg", min(r[1].cg_iters for r in rs), max(r[1].cg_iters for r in rs),
+          "; EP", min(r[2].nudged_iters[0] for r in rs), max(r[2].nudged_iters[0] for r in rs))
+    assert all(r[0].status in (0, 1) for r in rs)
+    assert all(r[1].status == 0 for r in rs)
+    tops = b.topologies()
+    Xs = b.split(X.cpu().numpy())
+    for k in (0, 37):
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=batch[k]["lam"])
+        top = dict(tops[k], vert=Xs[k])
+        F = omodel.forces(Xs[k], top, p)
+        fo = np.sqrt((F * F).sum(axis=1)).max()
+        E = omodel.energy(Xs[k], top, p)
+        fr, ra, re = rs[k]
+        C, _ = omodel.shape_tensor_anisotropy(Xs[k], top, (0.1, 0.0))
+        assert abs(fr.energy - E) < 1e-5 * abs(E)
+        assert abs(fo - fr.fmax) < 1e-2 * fr.fmax + 1e-7
+        assert abs(ra.cost - C) < 1e-8 * abs(C) + 1e-14
+        t = vx.Tissue(top, "f32")
+        g1, r1 = vx.vx_equilibrium_grad(t, Xs[k], p, cost=vx.VX_COST_ANISO,
+                                        cost_data=np.array([0.1, 0.0]), cg_rtol=1e-6)
+        t.close()
+        e0, e1 = b.ebase[k], b.ebase[k] + b.E[k]
+        ga_k, ge_k = ga["lam"][e0:e1].cpu().numpy(), ge["lam"][e0:e1].cpu().numpy()
+        e_single = rel(ga_k, g1["lam"].cpu().numpy())
+        e_ep = rel(ge_k, ga_k)
+        print(f"c5 tissue {k}: free {fr.status} {fr.iters} it fmax {fr.fmax:.1e} (oracle {fo:.1e}); "
+              f"batched vs single adjoint {e_single:.1e}; EP vs adjoint {e_ep:.1e}")
+        assert e_single < 1e-3
+        assert e_ep < 5e-2
+    b.close()
