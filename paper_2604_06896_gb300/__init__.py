@@ -577,12 +577,16 @@ def vx_equilibrium_grad_batched(b: Batch, Xstar, params, dCdX, cg_rtol=1e-10, cg
 
 
 def vx_batch_grad(b: Batch, X, params, cost, cost_data, what=3, free=None, mode=VX_EP_CENTERED,
-                  beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, inner=None, ep_f64=0):
+                  beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, inner=None, ep_f64=0,
+                  strict=True):
     """The batched gradient workload in one launch (see vx.h): relax every
     tissue (X: device f64 [sum V, 2], updated in place to X*), then the
     adjoint (what & 1) and / or EP (what & 2) gradients of the built-in
     cost.  Returns (adjoint dict, EP dict of device f64 tensors lam / A0 /
-    P0, list of (MinResult, adjoint GradResult, EP GradResult))."""
+    P0, list of (MinResult, adjoint GradResult, EP GradResult)).  A tissue
+    whose free relaxation ends in non-finite forces or an inconsistent
+    topology raises VxError unless strict=False, in which case the
+    per-tissue statuses report it."""
     torch = _torch()
     if not (hasattr(X, "is_cuda") and X.is_cuda and X.dtype == torch.float64
             and X.is_contiguous()):
@@ -607,7 +611,8 @@ def vx_batch_grad(b: Batch, X, params, cost, cost_data, what=3, free=None, mode=
                             _ptr(ga.get("lam")), _ptr(ga.get("A0")), _ptr(ga.get("P0")),
                             _ptr(ge.get("lam")), _ptr(ge.get("A0")), _ptr(ge.get("P0")), r,
                             _stream())
-    if st not in (capi.VX_OK, capi.VX_ERR_INDEFINITE):
+    per_tissue = (capi.VX_ERR_INDEFINITE, capi.VX_ERR_NONFINITE, capi.VX_ERR_TOPOLOGY)
+    if st != capi.VX_OK and (strict and st != capi.VX_ERR_INDEFINITE or st not in per_tissue):
         capi.check(st, "vx_batch_grad")
     out = []
     for x in r:

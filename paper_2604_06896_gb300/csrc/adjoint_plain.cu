@@ -515,21 +515,31 @@ __global__ void k_sen_rhs(View<P> v, ParamsD prm, int kind, int idx, double2* r)
   }
 }
 
-// out = -a.b (FP64, one block, fixed order).
+// out = -a.(Pi b) = -(sum a.b - (sum a).(sum b) / V): the solution b of a
+// singular solve carries an arbitrary rigid translation (the preconditioned
+// CG iterates leave the range of H), which the projection removes (FP64,
+// one block, fixed order).
 __global__ void k_neg_dot(int V, const double2* a, const double2* b, double* out) {
-  __shared__ double red[kT / 32];
-  double s = 0;
+  __shared__ double red[5][kT / 32];
+  double s[5] = {0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     const double2 x = a[i], y = b[i];
-    s += x.x * y.x + x.y * y.y;
+    s[0] += x.x * y.x + x.y * y.y;
+    s[1] += x.x;
+    s[2] += x.y;
+    s[3] += y.x;
+    s[4] += y.y;
   }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int q = 0; q < 5; ++q) {
+    const double w = warp_sum(s[q]);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = w;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    *out = -t;
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int q = 0; q < 5; ++q) t[q] += red[q][w];
+    *out = -(t[0] - (t[1] * t[3] + t[2] * t[4]) / V);
   }
 }
 
@@ -711,7 +721,8 @@ static vx_status adjoint_plain_t(vx_tissue_s* t, const double* Xstar, const Para
 
 // Forward sensitivity (Sen-ID): for each parameter theta_k, solve
 // H s_k = m_k with m_k = d(grad_X E)/d theta_k, then dC/d theta_k =
-// -grad_X C . s_k.  One solve per parameter.
+// -grad_X C . Pi s_k (Pi removes the rigid translation, along which H is
+// singular and X* undetermined).  One solve per parameter.
 template <class P>
 static vx_status sensitivity_t(vx_tissue_s* t, const double* Xstar, const ParamsD& prm,
                                const double* dCdX, int count, const int32_t* kind,

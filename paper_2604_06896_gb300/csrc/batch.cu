@@ -390,6 +390,8 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
     MinParams mpn = a.nud;
     if (mpn.cost == 1) mpn.cost_data = a.nud.cost_data + 2 * (size_t)d.vbase;  // X_target slice
     mpn.aniso_ws = mpn.cost == 2 ? (double*)acent : nullptr;
+    // the nudge reuses grad_X C's buffer: the adjoint has read it by then
+    mpn.aniso_nudge = mpn.cost == 2 ? (double*)dC : nullptr;
     double cost = 0.0;
     if (mpn.cost == 1) {
       double s1[1] = {0};
@@ -1359,10 +1361,19 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
     ge.cost = o.cost;
     ge.nudged_iters[0] = a.do_ep ? o.plus.iters : 0;
     ge.nudged_iters[1] = (a.do_ep && a.centered) ? o.minus.iters : 0;
-    if (ga.status == VX_ERR_INDEFINITE) worst = VX_ERR_INDEFINITE;
-    if (f.status == VX_ERR_NONFINITE || f.status == VX_ERR_TOPOLOGY) worst = (vx_status)f.status;
+    if (ga.status == VX_ERR_INDEFINITE && worst == VX_OK) {
+      worst = VX_ERR_INDEFINITE;
+      set_error("CG met a direction of non-positive curvature in tissue " + std::to_string(k) +
+                " (and possibly others)");
+    }
+    if ((f.status == VX_ERR_NONFINITE || f.status == VX_ERR_TOPOLOGY) &&
+        (worst == VX_OK || worst == VX_ERR_INDEFINITE)) {
+      worst = (vx_status)f.status;
+      set_error(std::string(f.status == VX_ERR_NONFINITE ? "non-finite forces"
+                                                         : "an inconsistent topology") +
+                " in the free relaxation of tissue " + std::to_string(k) +
+                " (and possibly others); the per-tissue results say which");
+    }
   }
-  if (worst == VX_ERR_INDEFINITE)
-    set_error("CG met a direction of non-positive curvature in at least one tissue");
   return worst;
 }

@@ -367,50 +367,9 @@ __device__ __forceinline__ int face_size(const View<P>& v, int h0) {
   return k;
 }
 
-// Cell energy K_A (A - A0)^2 + K_P (P - P0)^2 in float64 (for the T1
-// comparison).
-template <class P>
-__device__ double cell_energy_d(const View<P>& v, int c, const ParamsD& prm) {
-  const int h0 = v.ffirst[c];
-  const double2 X0 = P::to_d(v.X[src_of(v, h0)]);
-  double qx = 0, qy = 0, A2 = 0, pp = 0;
-  int cx = 0, cy = 0, h = h0, guard = 0;
-  do {
-    const uint32_t tg = v.tgt[h];
-    cx += tgt_ox(tg);
-    cy += tgt_oy(tg);
-    const double2 Xt = P::to_d(v.X[tgt_v(tg)]);
-    const double nx = (Xt.x + cx * v.Lx) - X0.x, ny = (Xt.y + cy * v.Ly) - X0.y;
-    A2 += qx * ny - nx * qy;
-    pp += sqrt((nx - qx) * (nx - qx) + (ny - qy) * (ny - qy));
-    qx = nx;
-    qy = ny;
-    h = v.nxt[h];
-  } while (h != h0 && ++guard < 4096);
-  const double A = 0.5 * A2, dA = A - prm.a0(c), dP = pp - prm.p0(c);
-  return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
-}
-
-// Local energies of the T1 comparison in the tissue's precision: FP64
-// tissues use the FP64 walks above; FP32 tissues take areas, perimeters and
-// lengths in FP32 from TwoSum-exact local differences (as the cell and
-// force passes do) and only combine them in FP64.  GB300 issues FP64 at a
-// small fraction of the FP32 rate, and a T1 candidate evaluates eight cell
-// energies and ten edge lengths.  The half-edge tables are walked (the flat
-// tables are stale during a trial).
-template <class P>
-__device__ double cell_energy_p(const View<P>& v, int c, const ParamsD& prm) {
-  if constexpr (std::is_same<typename P::R, double>::value) {
-    return cell_energy_d(v, c, prm);
-  } else {
-    View<P> w = v;
-    w.ccor = nullptr;
-    float A, Pp;
-    cell_geometry(w, c, A, Pp, 0.0f, (uint32_t*)nullptr);
-    const double dA = (double)A - prm.a0(c), dP = (double)Pp - prm.p0(c);
-    return prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
-  }
-}
+// Edge length in the tissue's precision (the T1 length checks): FP64
+// tissues in FP64, FP32 tissues in FP32 from the TwoSum-exact local
+// difference (as the cell and force passes do).
 template <class P>
 __device__ __forceinline__ double edge_len_p(const View<P>& v, int h) {
   if constexpr (std::is_same<typename P::R, double>::value) {
@@ -457,217 +416,6 @@ struct T1Stats {
 };
 
 constexpr double kT1Stretch = 1.5;  // both candidates: length 1.5 l_min
-
-// The T1 pass (Methods, "T1 transitions"), executed by the 32 lanes of one
-// warp: edges flagged in `shortbits` are taken in increasing id, each
-// re-checked against the current positions; for an edge shorter than lmin
-// the stretch and the T1 candidates (both of length 1.5 lmin about the old
-// midpoint) are compared by energy and the lower one kept.  A T1 is not a
-// candidate when a cell losing the edge is a triangle, when the four cells
-// are not distinct, when an offset would leave {-1, 0, 1} or when a cell
-// would outgrow the flat tables.  Edges with a larger id that a change makes
-// short are flagged and handled in the same pass.  Vertices of changed edges
-// are flagged in `touched` (their velocities are reset by the caller).
-// Clears `shortbits`.  Cells whose geometry changed are appended to `dirty`
-// (up to `dirty_cap`; `*n_dirty` may exceed it).  `events` (optional, [E][2])
-// counts the stretches and T1s of every edge.
-// Lane 0 does the bookkeeping and the writes; lanes 0..3 evaluate the four
-// cells and lanes 4..8 the five edges of a candidate in parallel (energies
-// summed with a fixed shuffle tree); the flat-table rebuild is spread over
-// lanes as well.  Every lane must call it.
-template <class P>
-__device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double lmin,
-                                          uint32_t* shortbits, uint32_t* touched, T1Stats* st,
-                                          int* dirty = nullptr, int dirty_cap = 0,
-                                          int* n_dirty = nullptr, int* events = nullptr) {
-  using Pos = typename P::Pos;
-  const int lane = threadIdx.x & 31;
-  const int nwords = (v.E + 31) >> 5;
-  const double lnew = kT1Stretch * lmin;
-  auto local_energy = [&](const int* cells, const int* hes) -> double {
-    double x = 0.0;
-    if (lane < 4) x = cell_energy_p(v, cells[lane], prm);
-    else if (lane < 9) x = prm.la(hes[lane - 4] >> 1) * edge_len_p(v, hes[lane - 4]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-  };
-  // The mask is scanned 128 words at a time (4 per lane, one coalesced
-  // load), and only words found non-zero are visited; once a join has set a
-  // bit further on in the chunk, the rest of the chunk is read word by word.
-  for (int w0 = 0; w0 < nwords; w0 += 128) {
-    uint32_t any = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = w0 + 4 * lane + q;
-      // generic loads: the mask lives in shared memory on the resident
-      // path and in global memory on the team paths
-      any |= idx < nwords ? ((volatile const uint32_t*)shortbits)[idx] : 0u;
-    }
-    const unsigned nz = __ballot_sync(0xffffffffu, any != 0);
-    bool joined = false;
-    const int wend = w0 + 128 < nwords ? w0 + 128 : nwords;
-  for (int w = w0; w < wend; ++w) {
-    if (!joined && !((nz >> ((w - w0) >> 2)) & 1u)) {
-      w |= 3;  // skip the rest of this lane's group of four words
-      continue;
-    }
-    for (;;) {
-      __syncwarp();
-      const uint32_t bits = ((volatile const uint32_t*)shortbits)[w];
-      if (!bits) break;
-      const int bit = __ffs(bits) - 1;
-      __syncwarp();
-      if (lane == 0) shortbits[w] = bits & (bits - 1);
-      __syncwarp();
-      const int e = (w << 5) + bit;
-      const int h = 2 * e, hq = h ^ 1;
-      if (edge_len_p(v, h) >= lmin) continue;
-      const int a = src_of(v, h), b = tgt_v(v.tgt[h]);
-      if (lane == 0) {
-        touched[a >> 5] |= 1u << (a & 31);
-        touched[b >> 5] |= 1u << (b & 31);
-      }
-      const int C1 = v.face[h], C2 = v.face[hq];
-      const int hp1 = prev_of(v, h), hn1 = v.nxt[h];
-      const int hp2 = prev_of(v, hq), hn2 = v.nxt[hq];
-      const int ta_p = hp1 ^ 1, tb_y = hn1 ^ 1, tb_z = hp2 ^ 1, tx_a = hn2 ^ 1;
-      const int C3 = v.face[ta_p], C4 = v.face[tb_z];
-      const int cells[4] = {C1, C2, C3, C4};
-      const int hes[5] = {h, hp1, hn1, hp2, hn2};
-      const uint32_t tg_h = v.tgt[h];
-      const int kbx = tgt_ox(tg_h), kby = tgt_oy(tg_h);
-      const int kpx = tgt_ox(v.tgt[ta_p]), kpy = tgt_oy(v.tgt[ta_p]);
-      const int kxx = tgt_ox(v.tgt[hn2]), kxy = tgt_oy(v.tgt[hn2]);
-      const int kyx = kbx + tgt_ox(v.tgt[hn1]), kyy = kby + tgt_oy(v.tgt[hn1]);
-      const int kzx = kbx + tgt_ox(v.tgt[tb_z]), kzy = kby + tgt_oy(v.tgt[tb_z]);
-      // face sizes of C1, C2, C3, C4 in parallel
-      const int fh[4] = {h, hq, ta_p, tb_z};
-      const int fs = lane < 4 ? face_size(v, fh[lane]) : 0;
-      const int s1 = __shfl_sync(0xffffffffu, fs, 0), s2 = __shfl_sync(0xffffffffu, fs, 1);
-      const int s3 = __shfl_sync(0xffffffffu, fs, 2), s4 = __shfl_sync(0xffffffffu, fs, 3);
-      const bool allow = s1 > 3 && s2 > 3 && (!v.ccor || (s3 < kMaxCorners && s4 < kMaxCorners)) &&
-                         C1 != C2 && C1 != C3 && C1 != C4 && C2 != C3 && C2 != C4 && C3 != C4 &&
-                         kyx >= -1 && kyx <= 1 && kyy >= -1 && kyy <= 1 && kzx >= -1 &&
-                         kzx <= 1 && kzy >= -1 && kzy <= 1;
-      double dx, dy;
-      edge_vec_d(v, h, dx, dy);
-      const double ell = sqrt(dx * dx + dy * dy);
-      const double ux = dx / ell, uy = dy / ell;
-      const double2 Xa = P::to_d(v.X[a]);
-      const double mx = Xa.x + 0.5 * dx, my = Xa.y + 0.5 * dy;
-      const Pos Xas = P::from_d(mx - 0.5 * lnew * ux, my - 0.5 * lnew * uy);
-      const Pos Xbs = P::from_d(mx + 0.5 * lnew * ux - kbx * v.Lx, my + 0.5 * lnew * uy - kby * v.Ly);
-      const int p = tgt_v(v.tgt[ta_p]), y = tgt_v(v.tgt[hn1]);
-      const int x = tgt_v(v.tgt[hn2]), z = tgt_v(v.tgt[tb_z]);
-      __syncwarp();
-      if (lane == 0) {
-        v.X[a] = Xas;
-        v.X[b] = Xbs;
-      }
-      __syncwarp();
-      const double Es = local_energy(cells, hes);
-      bool take_t1 = false;
-      if (allow) {
-        const int sv_nxt_i[6] = {hp1, hp2, tx_a, hq, tb_y, h};
-        const int sv_tgt_i[10] = {ta_p, hp1, hn1, tb_y, hn2, tx_a, tb_z, hp2, h, hq};
-        int sv_nxt[6];
-        uint32_t sv_tgt[10];
-        for (int k = 0; k < 6; ++k) sv_nxt[k] = v.nxt[sv_nxt_i[k]];
-        for (int k = 0; k < 10; ++k) sv_tgt[k] = v.tgt[sv_tgt_i[k]];
-        int sv_vout[6];
-        for (int k = 0; k < 3; ++k) {
-          sv_vout[k] = v.vout[k * v.V + a];
-          sv_vout[3 + k] = v.vout[k * v.V + b];
-        }
-        const int sv_ff[2] = {v.ffirst[C1], v.ffirst[C2]};
-        const double px = -uy, py = ux;  // into C1
-        __syncwarp();
-        if (lane == 0) {
-          v.X[a] = P::from_d(mx + 0.5 * lnew * px, my + 0.5 * lnew * py);
-          v.X[b] = P::from_d(mx - 0.5 * lnew * px, my - 0.5 * lnew * py);
-          v.nxt[hp1] = hn1;
-          v.nxt[hp2] = hn2;
-          v.nxt[tx_a] = hq;
-          v.nxt[hq] = ta_p;
-          v.nxt[tb_y] = h;
-          v.nxt[h] = tb_z;
-          v.face[hq] = C3;
-          v.face[h] = C4;
-          v.tgt[ta_p] = pack_tgt(p, kpx, kpy);
-          v.tgt[hp1] = pack_tgt(a, -kpx, -kpy);
-          v.tgt[hn1] = pack_tgt(y, kyx, kyy);
-          v.tgt[tb_y] = pack_tgt(a, -kyx, -kyy);
-          v.tgt[hn2] = pack_tgt(x, kxx, kxy);
-          v.tgt[tx_a] = pack_tgt(b, -kxx, -kxy);
-          v.tgt[tb_z] = pack_tgt(z, kzx, kzy);
-          v.tgt[hp2] = pack_tgt(b, -kzx, -kzy);
-          v.tgt[h] = pack_tgt(b, 0, 0);
-          v.tgt[hq] = pack_tgt(a, 0, 0);
-          v.vout[a] = h;
-          v.vout[v.V + a] = hn1;
-          v.vout[2 * v.V + a] = ta_p;
-          v.vout[b] = hq;
-          v.vout[v.V + b] = hn2;
-          v.vout[2 * v.V + b] = tb_z;
-          if (v.ffirst[C1] == h) v.ffirst[C1] = hn1;
-          if (v.ffirst[C2] == hq) v.ffirst[C2] = hn2;
-        }
-        __syncwarp();
-        const double Et = local_energy(cells, hes);
-        take_t1 = Et < Es;
-        __syncwarp();
-        if (!take_t1 && lane == 0) {
-          for (int k = 0; k < 6; ++k) v.nxt[sv_nxt_i[k]] = sv_nxt[k];
-          for (int k = 0; k < 10; ++k) v.tgt[sv_tgt_i[k]] = sv_tgt[k];
-          v.face[h] = C1;
-          v.face[hq] = C2;
-          for (int k = 0; k < 3; ++k) {
-            v.vout[k * v.V + a] = sv_vout[k];
-            v.vout[k * v.V + b] = sv_vout[3 + k];
-          }
-          v.ffirst[C1] = sv_ff[0];
-          v.ffirst[C2] = sv_ff[1];
-        }
-      }
-      __syncwarp();
-      if (lane == 0 && events) events[2 * e + (take_t1 ? 1 : 0)] += 1;
-      if (take_t1) {
-        if (lane == 0) st->n_t1++;
-        if (v.ccor) {
-          const int ws[6] = {a, b, p, x, y, z};
-          if (lane < 6) rebuild_vertex(v, ws[lane]);
-          else if (lane < 10) rebuild_cell(v, cells[lane - 6]);
-        }
-      } else if (lane == 0) {
-        v.X[a] = Xas;
-        v.X[b] = Xbs;
-        st->n_stretch++;
-      }
-      if (lane == 0 && n_dirty) {
-        for (int k = 0; k < 4; ++k) {
-          if (*n_dirty < dirty_cap) dirty[*n_dirty] = cells[k];
-          ++*n_dirty;
-        }
-      }
-      __syncwarp();
-      // Edges at a or b with a larger id that are now short join this pass.
-      bool join = false;
-      if (lane < 6) {
-        const int vv = lane < 3 ? a : b;
-        const int hh = v.vout[(lane % 3) * v.V + vv];
-        const int f = hh >> 1;
-        if (f > e && edge_len_p(v, hh) < lmin) {
-          atomicOr(&shortbits[f >> 5], 1u << (f & 31));
-          join = true;
-        }
-      }
-      joined |= __any_sync(0xffffffffu, join);
-    }
-  }
-  }
-  __syncwarp();
-}
 
 // ------------------------------------------------------------ wrap
 

@@ -148,6 +148,7 @@ MinParams nudged_params(const vx_grad_opts* o, vx_tissue_s* t) {
   mp.cost = o->cost;
   mp.cost_data = o->cost_data;
   mp.aniso_ws = o->cost == VX_COST_ANISO ? (double*)aniso_ws(t).cent : nullptr;
+  mp.aniso_nudge = o->cost == VX_COST_ANISO ? aniso_ws(t).gradX : nullptr;  // free in EP
   return mp;
 }
 

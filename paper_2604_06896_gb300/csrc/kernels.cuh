@@ -22,8 +22,10 @@ struct MinParams {
   double nudge_s;
   const double* cost_data;  // X_target [V][2] (v2v) or q_target [2] (anisotropy)
   // anisotropy nudging: per-cell centroids double2 [n] followed by corner
-  // counts int [n] (global memory, any residency)
+  // counts int [n], and the per-vertex nudge double2 [V] (global memory,
+  // any residency)
   double* aniso_ws;
+  double* aniso_nudge;
   // Exit-time wrap of positions and offsets (applied by the host launcher
   // after the solve).
   int wrap;

@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "device_math.cuh"
+#include "t1.cuh"
 #include "kernels.cuh"
 #include "tissue.h"
 

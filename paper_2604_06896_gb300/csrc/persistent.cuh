@@ -12,6 +12,7 @@
 #pragma once
 #include <type_traits>
 #include "device_math.cuh"
+#include "t1.cuh"
 #include "kernels.cuh"
 #include "team.cuh"
 
@@ -133,6 +134,38 @@ __device__ __forceinline__ void aniso_grad_vertex(const View<P>& v, int i, const
   }
 }
 
+// The anisotropy nudge of a nudged phase, out of line so that the solver
+// loops carry none of its registers: the shape tensors of the cells
+// c = first + k stride (partial Q into Q), then, after a team barrier has
+// published the centroids, grad_X C of the vertices i = first + k stride
+// into nudge[i].
+template <class P>
+__device__ __noinline__ void aniso_q_pass(View<P> v, int first, int stride, double* ws,
+                                          double* Q) {
+  double2* cent = (double2*)ws;
+  int* kk = (int*)(ws + 2 * (size_t)v.n);
+  Q[0] = Q[1] = Q[2] = 0;
+  for (int c = first; c < v.n; c += stride) {
+    double sxx, syy, sxy;
+    cell_shape(v, c, cent, kk, sxx, syy, sxy);
+    Q[0] += sxx;
+    Q[1] += syy;
+    Q[2] += sxy;
+  }
+}
+template <class P>
+__device__ __noinline__ void aniso_nudge_pass(View<P> v, int first, int stride, const double* ws,
+                                              double G0, double G1, double G2, double2* nudge) {
+  const double G[3] = {G0, G1, G2};
+  const double2* cent = (const double2*)ws;
+  const int* kk = (const int*)(ws + 2 * (size_t)v.n);
+  for (int i = first; i < v.V; i += stride) {
+    double gx, gy;
+    aniso_grad_vertex(v, i, cent, kk, G, gx, gy);
+    nudge[i] = make_double2(gx, gy);
+  }
+}
+
 // --------------------------------------------------------------- minimiser
 
 // Coefficients (cA, cP) of the listed cells, by the 32 lanes of one warp,
@@ -181,7 +214,8 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
   // centroid is conserved because every force term sums to zero).
   double nmx = 0, nmy = 0;
   const bool nudged = mp.cost == 1 && mp.nudge_s != 0.0;
-  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr;
+  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr &&
+                            mp.aniso_nudge != nullptr;
   if (nudged) {
     double s2[2] = {0, 0};
 #pragma unroll
@@ -260,23 +294,17 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     // dC/dQ from the team-wide mean Q (the reduction's barrier publishes the
     // centroids to the whole team; the nudged phases run without T1, so
     // bank c is free here).
-    double G[3] = {0, 0, 0};
     if (nudged_aniso) {
-      double2* cent = (double2*)mp.aniso_ws;
-      int* kk = (int*)(mp.aniso_ws + 2 * (size_t)n);
-      double Q[3] = {0, 0, 0};
-      for (int c = f0; c < n; c += st) {
-        double sxx, syy, sxy;
-        cell_shape(vw, c, cent, kk, sxx, syy, sxy);
-        Q[0] += sxx;
-        Q[1] += syy;
-        Q[2] += sxy;
-      }
+      double Q[3];
+      aniso_q_pass(vw, f0, st, mp.aniso_ws, Q);
       tm.template reduce<3>(Q, sl.c, 0);
       Q[0] /= n;
       Q[1] /= n;
       Q[2] /= n;
+      double G[3];
       aniso_dC_dQ(Q, mp.cost_data, G);
+      // each thread reads back only its own vertices' nudges
+      aniso_nudge_pass(vw, f0, st, mp.aniso_ws, G[0], G[1], G[2], (double2*)mp.aniso_nudge);
     }
     // F.F, F.v, v.v, max |F_i|^2: FP32 tissues sum their per-thread and
     // per-warp parts in FP32 and combine warps in FP64
@@ -300,11 +328,9 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
         }
         if (nudged_aniso) {
           // sum_i dC/dx_i = 0 (each cell's w sum to zero): no projection
-          double gx, gy;
-          aniso_grad_vertex(vw, i, (const double2*)mp.aniso_ws,
-                            (const int*)(mp.aniso_ws + 2 * (size_t)n), G, gx, gy);
-          fx[k] -= (R)(mp.nudge_s * gx);
-          fy[k] -= (R)(mp.nudge_s * gy);
+          const double2 g = ((const double2*)mp.aniso_nudge)[i];
+          fx[k] -= (R)(mp.nudge_s * g.x);
+          fy[k] -= (R)(mp.nudge_s * g.y);
         }
         if constexpr (kF32) {
           const float f2 = fx[k] * fx[k] + fy[k] * fy[k];
@@ -857,9 +883,8 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
   // of grad C taken once, the centroid being conserved; anisotropy: the
   // gradient sums to zero by itself).
   const bool nudged_v2v = mp.cost == 1 && mp.nudge_s != 0.0;
-  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr;
-  double2* acent = nudged_aniso ? (double2*)mp.aniso_ws : nullptr;
-  int* akk = nudged_aniso ? (int*)(mp.aniso_ws + 2 * (size_t)n) : nullptr;
+  const bool nudged_aniso = mp.cost == 2 && mp.nudge_s != 0.0 && mp.aniso_ws != nullptr &&
+                            mp.aniso_nudge != nullptr;
   double nmx = 0, nmy = 0;
   if (nudged_v2v) {
     double s2[2] = {0, 0};
@@ -921,21 +946,16 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     }
     // Nudged phases (no T1, so bank c is free): anisotropy dC/dQ from the
     // cells' shapes; the reduction's barrier publishes the centroids.
-    double G[3] = {0, 0, 0};
     if (nudged_aniso) {
-      double Q[3] = {0, 0, 0};
-      for (int c = tid; c < n; c += T) {
-        double sxx, syy, sxy;
-        cell_shape(vw, c, acent, akk, sxx, syy, sxy);
-        Q[0] += sxx;
-        Q[1] += syy;
-        Q[2] += sxy;
-      }
+      double Q[3];
+      aniso_q_pass(vw, tid, T, mp.aniso_ws, Q);
       tm.template reduce<3>(Q, sl.c, 0);
       Q[0] /= n;
       Q[1] /= n;
       Q[2] /= n;
+      double G[3];
       aniso_dC_dQ(Q, mp.cost_data, G);
+      aniso_nudge_pass(vw, tid, T, mp.aniso_ws, G[0], G[1], G[2], (double2*)mp.aniso_nudge);
     }
     double red[4] = {0, 0, 0, 0};
     for (int i = tid; i < V; i += T) {
@@ -948,10 +968,9 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
         fy -= (R)(mp.nudge_s * (gy - nmy));
       }
       if (nudged_aniso) {
-        double gx, gy;
-        aniso_grad_vertex(vw, i, acent, akk, G, gx, gy);
-        fx -= (R)(mp.nudge_s * gx);
-        fy -= (R)(mp.nudge_s * gy);
+        const double2 g = ((const double2*)mp.aniso_nudge)[i];
+        fx -= (R)(mp.nudge_s * g.x);
+        fy -= (R)(mp.nudge_s * g.y);
       }
       R2 f;
       f.x = fx;
