@@ -13,6 +13,7 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vx|reference]
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -429,6 +430,65 @@ def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None):
             "vs_plain_gpu_path": v_b / v_p}
 
 
+def bulk_forces_metric(vx, torch, peak, n=1_000_000, steps=10):
+    """Bulk energy + force evaluation (vx_energy_forces, FP32 tissue) of one
+    periodic Voronoi tissue of n cells (box sqrt(n), seeds in Hilbert order,
+    A0 = 1, p0 = 3.7, per-edge Lambda ~ U(0, 0.1)), L2 flushed before every
+    timed call; vertex-force evals/s and the roofline against the measured
+    HBM copy rate.  Algorithmic bytes per call (the call's own FP64
+    interface): X read 32 n + F write 32 n + the cell cycles 24 n + the
+    per-edge Lambda (3 n edges x 8 B) 24 n = 112 n."""
+    seeds = vi.uniform_seeds(n, math.sqrt(n), math.sqrt(n), vi.substream(9, 0))
+    L = math.sqrt(n)
+    order = vx.vx_seed_order(seeds, L, L)
+    mesh = vx.vx_build_mesh(seeds[order], L, L)
+    t = vx.Tissue(mesh, "f32")
+    lam = torch.tensor(vi.SplitMix64(10).uniform(t.E, 0.0, 0.1), device="cuda")
+    p = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=lam)
+    X = torch.tensor(mesh["vert"], dtype=torch.float64, device="cuda")
+    F = torch.empty_like(X)
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prm, keep = vx.make_params(p, t.n, t.E)
+
+    def call():
+        st = vx.capi.vx_energy_forces(t.handle, X.data_ptr(), ctypes.byref(prm), F.data_ptr(),
+                                      E.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        vx.capi.check(st, "vx_energy_forces")
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            call()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):    # one replay = one call, without host launch gaps
+        call()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    med = float(np.median(ms))
+    achieved = 112.0 * n / (med * 1e-3) / 1e9
+    out = {"metric": "vertex-force evals/s", "unit": "vertex-force evals/s",
+           "value": t.V / (med * 1e-3), "ms_per_call": med,
+           "workload": f"one {n}-cell periodic Voronoi tissue ({t.V} vertices), FP32 hi/lo, "
+                       "per-edge Lambda, energy + forces per call (vx_energy_forces), L2 flushed "
+                       f"(256 MiB write) before every call, median of {steps} graph-replayed calls",
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "bytes_per_call": "112 n",
+                        "kernels": "k_load_X, k_cells, k_vertices, k_sum_energy"}}
+    t.close()
+    return out
+
+
 def c2_oracle_errors(finals):
     """The oracle's energy and max |F| at each c2 relaxation's returned state
     (GPU energy relative error, GPU max |F| against the oracle's)."""
@@ -576,6 +636,8 @@ def run_gpu(args):
               for p0, cs, r in zip(vi.C2_P0_SWEEP, cases, rs)]
 
     grad, grad_check = grad_metric(vx, torch, steps=max(1, args.steps), warmup=1)
+    bulk = None if args.no_batch else bulk_forces_metric(vx, torch, peak, n=args.bulk_cells,
+                                                         steps=args.bulk_steps)
     batched = None if args.no_batch else batched_forward_metric(vx, torch, steps=1)
     batched_grad = None if args.no_batch else batched_gradient_metric(vx, torch)
 
@@ -625,6 +687,7 @@ def run_gpu(args):
                              "per launch, one ncu capture) is null until the changed kernel is "
                              "captured again"},
         "equilibrium_gradient": grad,
+        "bulk_forces": bulk,
         "batched_forward": batched,
         "batched_gradient": batched_grad,
         "clocks": clk.summary(),
@@ -717,7 +780,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vx", choices=["vx", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched c3 line")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched c3 / c5 lines and the bulk force line")
+    ap.add_argument("--bulk-only", action="store_true",
+                    help="only the bulk energy + force line (for ncu)")
+    ap.add_argument("--bulk-cells", type=int, default=1_000_000)
+    ap.add_argument("--bulk-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
     ap.add_argument("--profile-iters", type=int, default=2000)
     ap.add_argument("--ordered", type=int, default=1, help="profile: Hilbert-ordered seeds")
@@ -727,6 +795,13 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.bulk_only:
+        import torch
+        import paper_2604_06896_gb300 as vx
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        print(json.dumps(bulk_forces_metric(vx, torch, peak, n=args.bulk_cells,
+                                            steps=args.bulk_steps)))
     elif args.impl == "reference":
         run_reference(args)
     else:

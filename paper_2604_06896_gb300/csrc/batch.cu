@@ -42,6 +42,11 @@ struct vx_batch_s {
   int32_t *nxt, *face, *vout, *ffirst;
   uint32_t* tgt0;
   int32_t *nxt0, *face0, *vout0, *ffirst0;
+  // flat tables of the L2-resident tissues (per vertex the packed targets
+  // and faces of its out-half-edges [3][V]; per cell its corner count,
+  // corners and half-edges [n][16]), rebuilt on every topology change
+  uint32_t *vnb, *ccor;
+  int32_t *vfc, *ccnt, *cedge;
   void *Xw, *vel, *frc, *cellc;
   uint32_t *shortbits, *touched;
   vx::MinOut* d_out;
@@ -82,12 +87,32 @@ struct BatchArgs {
   double* Xout;
   uint32_t* tgt;
   int32_t *nxt, *face, *vout, *ffirst;
+  uint32_t *vnb, *ccor;
+  int32_t *vfc, *ccnt, *cedge;
   void *Xw, *vel, *frc, *cellc;
   uint32_t *shortbits, *touched;
   const double *KA, *KP, *A0, *P0, *lam;  // per cell / per edge or null
   MinParams mp;
   MinOut* out;
 };
+
+// The flat-table pointers of tissue d (global memory).
+template <class P, class A>
+__device__ __forceinline__ void batch_flat(const A& g, const BatchDesc& d, View<P>& v) {
+  v.vnb = g.vnb + 3 * (size_t)d.vbase;
+  v.vfc = g.vfc + 3 * (size_t)d.vbase;
+  v.ccnt = g.ccnt + d.cbase;
+  v.ccor = g.ccor + (size_t)kMaxCorners * d.cbase;
+  v.cedge = g.cedge + (size_t)kMaxCorners * d.cbase;
+}
+
+// Rebuild the flat tables of one tissue from its half-edge tables (all
+// threads of the CTA; the caller synchronises before and after).
+template <class P>
+__device__ __forceinline__ void batch_rebuild_flat(const View<P>& v) {
+  for (int w = threadIdx.x; w < v.V; w += blockDim.x) rebuild_vertex(v, w);
+  for (int c = threadIdx.x; c < v.n; c += blockDim.x) rebuild_cell(v, c);
+}
 
 __host__ __device__ inline size_t b16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -186,6 +211,16 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
       }
       for (int q = tid; q < 3 * d.V; q += T) gv[q] = v.vout[q];
       for (int c = tid; c < d.n; c += T) gff[c] = v.ffirst[c];
+      __syncthreads();
+      // the global flat tables follow the topology the solve left
+      View<P> vg = v;
+      vg.tgt = gt;
+      vg.nxt = gn;
+      vg.face = gf;
+      vg.vout = gv;
+      vg.ffirst = gff;
+      batch_flat(g, d, vg);
+      batch_rebuild_flat(vg);
     } else {
       v.X = (Pos*)g.Xw + d.vbase;
       v.tgt = gt;
@@ -193,6 +228,7 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
       v.face = gf;
       v.vout = gv;
       v.ffirst = gff;
+      batch_flat(g, d, v);
       Slots sl = {gslots[0], gslots[1], gslots[2]};
       min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
                          prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xin,
@@ -211,6 +247,8 @@ struct BatchAdjArgs {
   const double* dCdX;  // [V_tot][2]
   uint32_t* tgt;
   int32_t *nxt, *face, *vout, *ffirst;
+  uint32_t *vnb, *ccor;
+  int32_t *vfc, *ccnt, *cedge;
   void *Xw, *cell4, *x, *r, *p, *z, *pre;
   const double *KA, *KP, *A0, *P0, *lam;
   double rtol;
@@ -265,6 +303,7 @@ __global__ void __launch_bounds__(T) k_adj_batch(BatchAdjArgs g) {
     v.face = g.face + d.hbase;
     v.vout = g.vout + 3 * d.vbase;
     v.ffirst = g.ffirst + d.cbase;
+    batch_flat(g, d, v);
     Slots sl = {slots[0], slots[1], slots[2]};
     adj_body_mem<P, T>(v, (R4*)g.cell4 + d.cbase, (R2*)g.x + d.vbase, (R2*)g.r + d.vbase,
                        (R2*)g.p + d.vbase, (R2*)g.z + d.vbase, (R4*)g.pre + d.vbase, prm.lam, sl,
@@ -300,11 +339,7 @@ struct BatchGradArgs {
 template <class P>
 __device__ __forceinline__ View<P> batch_view(const BatchArgs& g, const BatchDesc& d, void* X) {
   View<P> v;
-  v.vnb = nullptr;
-  v.vfc = nullptr;
-  v.ccnt = nullptr;
-  v.ccor = nullptr;
-  v.cedge = nullptr;
+  batch_flat(g, d, v);
   v.n = d.n;
   v.V = d.V;
   v.E = d.E;
@@ -335,11 +370,93 @@ __device__ __forceinline__ ParamsD batch_params(const BatchArgs& g, const BatchD
   return prm;
 }
 
+// The phases of one tissue's gradient, each out of line so that every
+// phase gets its own register allocation (the kernel calls them once per
+// tissue).
+
+// Free relaxation to X* (T1 on, per the free options); X* into Xk.
+template <class P, int T>
+__device__ __noinline__ void grad_free(const BatchGradArgs& a, const BatchDesc& d,
+                                       const ParamsD& prm, Slots sl, double* Xk, MinOut* out) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  const BatchArgs& g = a.b;
+  View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
+  min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+                     prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xk, Xk,
+                     out);
+  __syncthreads();
+}
+
+// The outer cost and grad_X C at X* (FP64, on the returned positions):
+// v2v, or the anisotropy with the cells' centroids and corner counts left in
+// acent / akk for the nudged phases.  Returns the cost (thread 0).
+template <int T>
+__device__ __noinline__ double grad_cost(const BatchGradArgs& a, const BatchDesc& d,
+                                         const MinParams& mpn, Slots sl, double* Xk,
+                                         double2* dC, double2* acent, int* akk) {
+  BlockTeam<T> tm;
+  const int tid = threadIdx.x;
+  View<PolF64> vs = batch_view<PolF64>(a.b, d, Xk);
+  double cost = 0.0;
+  if (mpn.cost == 1) {
+    double s1[1] = {0};
+    for (int i = tid; i < d.V; i += T) {
+      double gx, gy;
+      v2v_grad(vs, i, mpn.cost_data, gx, gy);
+      dC[i] = make_double2(gx, gy);
+      s1[0] += 0.5 * d.V * (gx * gx + gy * gy);
+    }
+    tm.template reduce<1>(s1, sl.a, 0);
+    cost = s1[0];
+  } else {
+    double Q[3] = {0, 0, 0};
+    for (int c = tid; c < d.n; c += T) {
+      double sxx, syy, sxy;
+      cell_shape(vs, c, acent, akk, sxx, syy, sxy);
+      Q[0] += sxx;
+      Q[1] += syy;
+      Q[2] += sxy;
+    }
+    tm.template reduce<3>(Q, sl.a, 0);
+    for (int q = 0; q < 3; ++q) Q[q] /= d.n;
+    double G[3];
+    aniso_dC_dQ(Q, mpn.cost_data, G);
+    const double T_ = Q[0] + Q[1];
+    const double q1 = (Q[0] - Q[1]) / T_ - mpn.cost_data[0];
+    const double q2 = 2.0 * Q[2] / T_ - mpn.cost_data[1];
+    cost = q1 * q1 + q2 * q2;
+    for (int i = tid; i < d.V; i += T) {
+      double gx, gy;
+      aniso_grad_vertex(vs, i, acent, akk, G, gx, gy);
+      dC[i] = make_double2(gx, gy);
+    }
+  }
+  __syncthreads();
+  return cost;
+}
+
+// The adjoint: H lam = Pi grad_X C by preconditioned CG, then
+// g = -(d2E/dX dth)^T lam.
+template <class P, int T>
+__device__ __noinline__ void grad_adjoint(const BatchGradArgs& a, const BatchDesc& d,
+                                          const ParamsD& prm, Slots sl, const double* Xk,
+                                          const double2* dC, AdjOut* out) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  using R4 = typename Vec2Of<typename P::R>::T4;
+  View<P> v = batch_view<P>(a.b, d, (typename P::Pos*)a.b.Xw + d.vbase);
+  adj_body_mem<P, T>(v, (R4*)a.cell4 + d.cbase, (R2*)a.ax + d.vbase, (R2*)a.ar + d.vbase,
+                     (R2*)a.ap + d.vbase, (R2*)a.az + d.vbase, (R4*)a.apre + d.vbase, prm.lam, sl,
+                     prm, (const double*)dC, a.rtol, a.cg_max_iter, Xk,
+                     a.ga_lam ? a.ga_lam + d.ebase : nullptr, a.ga_A0 ? a.ga_A0 + d.cbase : nullptr,
+                     a.ga_P0 ? a.ga_P0 + d.cbase : nullptr, out);
+  __syncthreads();
+}
+
 // One nudged phase from X* (positions in `Xs`) into Xout, in precision Q.
 template <class Q, int T>
-__device__ void batch_nudged(const BatchGradArgs& a, const BatchDesc& d, const ParamsD& prm,
-                             MinParams mp, double s, const double* Xs, double* Xout, Slots sl,
-                             MinOut* out) {
+__device__ __noinline__ void batch_nudged(const BatchGradArgs& a, const BatchDesc& d,
+                                          const ParamsD& prm, MinParams mp, double s,
+                                          const double* Xs, double* Xout, Slots sl, MinOut* out) {
   using R2 = typename Vec2Of<typename Q::R>::T;
   const BatchArgs& g = a.b;
   View<Q> v = batch_view<Q>(g, d, (typename Q::Pos*)g.Xw + d.vbase);
@@ -350,16 +467,33 @@ __device__ void batch_nudged(const BatchGradArgs& a, const BatchDesc& d, const P
   __syncthreads();
 }
 
+// EP: (d_theta E(X+) - d_theta E(X-)) / beta in FP64.
+template <int T>
+__device__ __noinline__ void grad_ep_diff(const BatchGradArgs& a, const BatchDesc& d,
+                                          const ParamsD& prm, const double* Xp,
+                                          const double* Xm) {
+  const int tid = threadIdx.x;
+  View<PolF64> vp = batch_view<PolF64>(a.b, d, (void*)Xp);
+  View<PolF64> vm = batch_view<PolF64>(a.b, d, (void*)Xm);
+  if (a.ge_lam)
+    for (int e = tid; e < d.E; e += T)
+      a.ge_lam[d.ebase + e] = (edge_len_d(vp, 2 * e) - edge_len_d(vm, 2 * e)) / a.beta;
+  if (a.ge_A0 || a.ge_P0)
+    for (int c = tid; c < d.n; c += T) {
+      double Ap, Pp, Am, Pm;
+      cell_geometry(vp, c, Ap, Pp, 0.0, nullptr);
+      cell_geometry(vm, c, Am, Pm, 0.0, nullptr);
+      if (a.ge_A0) a.ge_A0[d.cbase + c] = -2.0 * prm.ka(c) * (Ap - Am) / a.beta;
+      if (a.ge_P0) a.ge_P0[d.cbase + c] = -2.0 * prm.kp(c) * (Pp - Pm) / a.beta;
+    }
+  __syncthreads();
+}
+
 template <class P, int T>
 __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
-  using R = typename P::R;
-  using R2 = typename Vec2Of<R>::T;
-  using R4 = typename Vec2Of<R>::T4;
   __shared__ int item;
   __shared__ double slots[3][4 * (T / 32 + 1)];
-  __shared__ double Gs[3];
   const BatchArgs& g = a.b;
-  BlockTeam<T> tm;
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) item = atomicAdd(g.counter, 1);
@@ -373,16 +507,9 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
     BatchGradOut* o = a.out + tk;
     Slots sl = {slots[0], slots[1], slots[2]};
     double* Xk = (double*)g.X + 2 * (size_t)d.vbase;
-    // 1. the free equilibrium X* (T1 on, per the free options)
-    {
-      View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
-      min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
-                         prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xk, Xk,
-                         &o->free);
-      __syncthreads();
-    }
-    // 2. the outer cost and grad_X C at X* (FP64, on the returned positions)
-    View<PolF64> vs = batch_view<PolF64>(g, d, Xk);
+    // 1. the free equilibrium X*
+    grad_free<P, T>(a, d, prm, sl, Xk, &o->free);
+    // 2. the outer cost and grad_X C at X*
     double2* dC = (double2*)a.dC + d.vbase;
     // per tissue 4 n doubles (even offsets: the centroids are double2)
     double2* acent = (double2*)(a.aws + 4 * (size_t)d.cbase);
@@ -392,53 +519,10 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
     mpn.aniso_ws = mpn.cost == 2 ? (double*)acent : nullptr;
     // the nudge reuses grad_X C's buffer: the adjoint has read it by then
     mpn.aniso_nudge = mpn.cost == 2 ? (double*)dC : nullptr;
-    double cost = 0.0;
-    if (mpn.cost == 1) {
-      double s1[1] = {0};
-      for (int i = tid; i < d.V; i += T) {
-        double gx, gy;
-        v2v_grad(vs, i, mpn.cost_data, gx, gy);
-        dC[i] = make_double2(gx, gy);
-        s1[0] += 0.5 * d.V * (gx * gx + gy * gy);
-      }
-      tm.template reduce<1>(s1, sl.a, 0);
-      cost = s1[0];
-    } else {
-      double Q[3] = {0, 0, 0};
-      for (int c = tid; c < d.n; c += T) {
-        double sxx, syy, sxy;
-        cell_shape(vs, c, acent, akk, sxx, syy, sxy);
-        Q[0] += sxx;
-        Q[1] += syy;
-        Q[2] += sxy;
-      }
-      tm.template reduce<3>(Q, sl.a, 0);
-      for (int q = 0; q < 3; ++q) Q[q] /= d.n;
-      double G[3];
-      aniso_dC_dQ(Q, mpn.cost_data, G);
-      const double T_ = Q[0] + Q[1];
-      const double q1 = (Q[0] - Q[1]) / T_ - mpn.cost_data[0];
-      const double q2 = 2.0 * Q[2] / T_ - mpn.cost_data[1];
-      cost = q1 * q1 + q2 * q2;
-      for (int i = tid; i < d.V; i += T) {
-        double gx, gy;
-        aniso_grad_vertex(vs, i, acent, akk, G, gx, gy);
-        dC[i] = make_double2(gx, gy);
-      }
-    }
+    const double cost = grad_cost<T>(a, d, mpn, sl, Xk, dC, acent, akk);
     if (tid == 0) o->cost = cost;
-    __syncthreads();
-    // 3. the adjoint: H lam = Pi grad_X C by preconditioned CG, g = -(d2E/dX dth)^T lam
-    if (a.do_adjoint) {
-      View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
-      adj_body_mem<P, T>(v, (R4*)a.cell4 + d.cbase, (R2*)a.ax + d.vbase, (R2*)a.ar + d.vbase,
-                         (R2*)a.ap + d.vbase, (R2*)a.az + d.vbase, (R4*)a.apre + d.vbase, prm.lam,
-                         sl, prm, (const double*)dC, a.rtol, a.cg_max_iter, Xk,
-                         a.ga_lam ? a.ga_lam + d.ebase : nullptr,
-                         a.ga_A0 ? a.ga_A0 + d.cbase : nullptr,
-                         a.ga_P0 ? a.ga_P0 + d.cbase : nullptr, &o->adj);
-      __syncthreads();
-    }
+    // 3. the adjoint
+    if (a.do_adjoint) grad_adjoint<P, T>(a, d, prm, sl, Xk, dC, &o->adj);
     // 4. equilibrium propagation: E +/- (beta/2) C from X*, then the
     //    difference of d_theta E over beta
     if (a.do_ep) {
@@ -452,21 +536,8 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
         batch_nudged<P, T>(a, d, prm, mpn, sp, Xk, Xp, sl, &o->plus);
         if (a.centered) batch_nudged<P, T>(a, d, prm, mpn, -sp, Xk, Xm, sl, &o->minus);
       }
-      View<PolF64> vp = batch_view<PolF64>(g, d, Xp);
-      View<PolF64> vm = batch_view<PolF64>(g, d, a.centered ? Xm : Xk);
-      if (a.ge_lam)
-        for (int e = tid; e < d.E; e += T)
-          a.ge_lam[d.ebase + e] = (edge_len_d(vp, 2 * e) - edge_len_d(vm, 2 * e)) / a.beta;
-      if (a.ge_A0 || a.ge_P0)
-        for (int c = tid; c < d.n; c += T) {
-          double Ap, Pp, Am, Pm;
-          cell_geometry(vp, c, Ap, Pp, 0.0, nullptr);
-          cell_geometry(vm, c, Am, Pm, 0.0, nullptr);
-          if (a.ge_A0) a.ge_A0[d.cbase + c] = -2.0 * prm.ka(c) * (Ap - Am) / a.beta;
-          if (a.ge_P0) a.ge_P0[d.cbase + c] = -2.0 * prm.kp(c) * (Pp - Pm) / a.beta;
-        }
+      grad_ep_diff<T>(a, d, prm, Xp, a.centered ? Xm : Xk);
     }
-    (void)Gs;
     __syncthreads();
   }
 }
@@ -555,17 +626,25 @@ __global__ void k_aniso_batch(const BatchDesc* desc, int count, const uint32_t* 
   }
 }
 
+// The flat tables of every tissue from its half-edge tables (one CTA per
+// tissue at a time).
+__global__ void k_flat_batch(BatchArgs g) {
+  for (int k = blockIdx.x; k < g.count; k += gridDim.x) {
+    batch_rebuild_flat(batch_view<PolF64>(g, g.desc[k], nullptr));
+    __syncthreads();
+  }
+}
+
 // Exit-time wrap of every tissue (Methods, "Periodic mode"): positions back
 // into the tissue's box, offsets fixed so that the unwrapped edge vectors
 // keep their values.  One CTA per tissue at a time; an offset that would
 // leave {-1, 0, 1} is left unchanged and flagged in the tissue's result.
-__global__ void k_wrap_batch(const BatchDesc* desc, int count, double* X, uint32_t* tgt, int2* kv,
-                             MinOut* out) {
-  for (int k = blockIdx.x; k < count; k += gridDim.x) {
-    const BatchDesc d = desc[k];
+__global__ void k_wrap_batch(BatchArgs g, double* X, int2* kv, MinOut* out) {
+  for (int k = blockIdx.x; k < g.count; k += gridDim.x) {
+    const BatchDesc d = g.desc[k];
     double* Xk = X + 2 * (size_t)d.vbase;
     int2* kk = kv + d.vbase;
-    uint32_t* tk = tgt + d.hbase;
+    uint32_t* tk = g.tgt + d.hbase;
     for (int i = threadIdx.x; i < d.V; i += blockDim.x) {
       int kx, ky;
       Xk[2 * i] = wrap_coord(Xk[2 * i], d.Lx, kx);
@@ -584,6 +663,9 @@ __global__ void k_wrap_batch(const BatchDesc* desc, int count, double* X, uint32
       tk[2 * e] = pack_tgt(b, ox, oy);
       tk[2 * e + 1] = pack_tgt(a, -ox, -oy);
     }
+    __syncthreads();
+    // the packed targets and corner images of the flat tables carry offsets
+    batch_rebuild_flat(batch_view<PolF64>(g, d, Xk));
     __syncthreads();
   }
 }
@@ -752,6 +834,11 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   A((void**)&b->face0, 4 * (size_t)hb);
   A((void**)&b->vout0, 12 * (size_t)vb);
   A((void**)&b->ffirst0, 4 * (size_t)nb);
+  A((void**)&b->vnb, 12 * (size_t)vb);
+  A((void**)&b->vfc, 12 * (size_t)vb);
+  A((void**)&b->ccnt, 4 * (size_t)nb);
+  A((void**)&b->ccor, 4 * (size_t)vx::kMaxCorners * nb);
+  A((void**)&b->cedge, 4 * (size_t)vx::kMaxCorners * nb);
   A(&b->Xw, 16 * (size_t)vb);
   A(&b->vel, 16 * (size_t)vb);
   A(&b->frc, 16 * (size_t)vb);
@@ -801,7 +888,7 @@ vx_status vx_batch_destroy(vx_batch b) {
                   b->ffirst, b->tgt0,    b->nxt0,      b->face0, b->vout0, b->ffirst0, b->Xw,
                   b->vel,    b->frc,     b->cellc,     b->shortbits, b->touched, b->d_out,
                   b->adj_ws, b->d_adj_out, b->wrapk, b->aniso_ws, b->Xtune, b->gXp, b->gXm,
-                  b->gdC, b->gaws, b->gout};
+                  b->gdC, b->gaws, b->gout, b->vnb, b->vfc, b->ccnt, b->ccor, b->cedge};
   if (b->gexec2) cudaGraphExecDestroy(b->gexec2);
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -818,6 +905,26 @@ vx_status vx_batch_restore(vx_batch b, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->face, b->face0, 4 * hb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->vout, b->vout0, 12 * vb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->ffirst, b->ffirst0, 4 * nb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    vx::BatchArgs a = {};
+    a.desc = b->d_desc;
+    a.count = b->count;
+    a.tgt = b->tgt;
+    a.nxt = b->nxt;
+    a.face = b->face;
+    a.vout = b->vout;
+    a.ffirst = b->ffirst;
+    a.vnb = b->vnb;
+    a.vfc = b->vfc;
+    a.ccnt = b->ccnt;
+    a.ccor = b->ccor;
+    a.cedge = b->cedge;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    vx::k_flat_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
   return e == cudaSuccess ? VX_OK : fail(VX_ERR_CUDA, cudaGetErrorString(e));
 }
 
@@ -886,6 +993,11 @@ vx::BatchArgs make_batch_args(vx_batch b, double* X, const vx_batch_params* p, c
   a.face = b->face;
   a.vout = b->vout;
   a.ffirst = b->ffirst;
+  a.vnb = b->vnb;
+  a.vfc = b->vfc;
+  a.ccnt = b->ccnt;
+  a.ccor = b->ccor;
+  a.cedge = b->cedge;
   a.Xw = b->Xw;
   a.vel = b->vel;
   a.frc = b->frc;
@@ -932,8 +1044,7 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
     e = f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
             : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
     if (e != cudaSuccess || !mp.wrap) return e;
-    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(b->d_desc, b->count, X, b->tgt,
-                                                              b->wrapk, b->d_out);
+    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(a, X, b->wrapk, b->d_out);
     return cudaGetLastError();
   };
   cudaError_t e;
@@ -1117,6 +1228,11 @@ vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_
   a.face = b->face;
   a.vout = b->vout;
   a.ffirst = b->ffirst;
+  a.vnb = b->vnb;
+  a.vfc = b->vfc;
+  a.ccnt = b->ccnt;
+  a.ccor = b->ccor;
+  a.cedge = b->cedge;
   a.Xw = b->Xw;
   a.cell4 = w;
   a.x = w + o_x;
@@ -1291,8 +1407,7 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
       vx::k_grad_batch<vx::PolF32, 256><<<grid, 256, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess || !a.b.mp.wrap) return e;
-    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, st>>>(b->d_desc, b->count, X, b->tgt,
-                                                               b->wrapk, b->d_out);
+    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, st>>>(a.b, X, b->wrapk, b->d_out);
     return cudaGetLastError();
   };
   // Replay the captured launch when the arguments are unchanged.

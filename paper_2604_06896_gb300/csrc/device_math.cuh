@@ -256,6 +256,88 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
   return flagged;
 }
 
+// What the geometry of one cell reads from the flat tables, loaded in one go
+// (gather) and used afterwards (compute), so that a thread owning several
+// cells has all their loads in flight together: the corner count, the first
+// kGather corner words (two 16-byte loads) and their positions.  Corner
+// words past the count are clamped into [0, V) before use as indices; their
+// positions are loaded but never used.
+constexpr int kGather = 8;
+template <class P>
+struct CGather {
+  int m;
+  uint32_t w[kGather];
+  typename P::Pos X[kGather];
+};
+
+template <class P>
+__device__ __forceinline__ void cell_gather(const View<P>& v, int c, CGather<P>& g) {
+  g.m = v.ccnt[c];
+  const uint4* row = reinterpret_cast<const uint4*>(v.ccor + (size_t)c * kMaxCorners);
+  const uint4 a = row[0], b = row[1];
+  g.w[0] = a.x; g.w[1] = a.y; g.w[2] = a.z; g.w[3] = a.w;
+  g.w[4] = b.x; g.w[5] = b.y; g.w[6] = b.z; g.w[7] = b.w;
+#pragma unroll
+  for (int k = 0; k < kGather; ++k) g.X[k] = v.X[min(tgt_v(g.w[k]), v.V - 1)];
+}
+
+// cell_geometry's flat-table arithmetic, in the same order, from a gather
+// (corners past kGather are loaded here).
+template <class P>
+__device__ __forceinline__ bool cell_geometry_g(const View<P>& v, int c, const CGather<P>& g,
+                                                typename P::R& A, typename P::R& Per,
+                                                typename P::R lmin, uint32_t* shortbits,
+                                                double* eline = nullptr,
+                                                const ParamsD* prm = nullptr) {
+  using R = typename P::R;
+  const int m = g.m;
+  const int32_t* ced = v.cedge + (size_t)c * kMaxCorners;
+  R qx = 0, qy = 0, A2 = 0, pp = 0;
+  bool flagged = false;
+  double el = 0.0;
+  auto edge = [&](int kk, R nx, R ny) {
+    A2 += qx * ny - nx * qy;
+    const R ex = nx - qx, ey = ny - qy;
+    const R l = sqrt(ex * ex + ey * ey);
+    pp += l;
+    if (l < lmin) {
+      const int h = ced[kk];
+      atomicOr(&shortbits[h >> 6], 1u << ((h >> 1) & 31));
+      flagged = true;
+    }
+    if (eline) el += 0.5 * prm->la(ced[kk] >> 1) * (double)l;
+    qx = nx;
+    qy = ny;
+  };
+#pragma unroll
+  for (int kk = 0; kk < kGather; ++kk) {
+    if (kk < m) {
+      R nx = 0, ny = 0;
+      if (kk + 1 < m) {
+        if (kk + 1 < kGather) {
+          P::diff(g.X[kk + 1], g.X[0], tgt_ox(g.w[kk + 1]), tgt_oy(g.w[kk + 1]), v.box, nx, ny);
+        } else {
+          const uint32_t t = v.ccor[(size_t)c * kMaxCorners + kk + 1];
+          P::diff(v.X[tgt_v(t)], g.X[0], tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+        }
+      }
+      edge(kk, nx, ny);
+    }
+  }
+  for (int kk = kGather; kk < m; ++kk) {
+    R nx = 0, ny = 0;
+    if (kk + 1 < m) {
+      const uint32_t t = v.ccor[(size_t)c * kMaxCorners + kk + 1];
+      P::diff(v.X[tgt_v(t)], g.X[0], tgt_ox(t), tgt_oy(t), v.box, nx, ny);
+    }
+    edge(kk, nx, ny);
+  }
+  A = (R)0.5 * A2;
+  Per = pp;
+  if (eline) *eline = el;
+  return flagged;
+}
+
 // Everything the force on one vertex reads, loaded in one go (gather) and
 // used afterwards (compute), so that a thread owning several vertices has
 // all their loads in flight together.

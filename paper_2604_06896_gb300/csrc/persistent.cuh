@@ -239,6 +239,32 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
 
   auto cell_pass = [&](R lm) -> bool {
     bool fl = false;
+    if (vw.ccor) {
+      // owned cells in pairs, both gathers in flight before either is used
+      // (flat tables)
+#pragma unroll
+      for (int k0 = 0; k0 < MAXC; k0 += 2) {
+        CGather<P> g[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = f0 + (k0 + j) * st;
+          if (k0 + j < MAXC && c < n) cell_gather(vw, c, g[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = f0 + (k0 + j) * st;
+          if (k0 + j < MAXC && c < n) {
+            R A, Pp;
+            fl |= cell_geometry_g(vw, c, g[j], A, Pp, lm, shortbits);
+            R2 cc;
+            cc.x = (R)2 * (R)prm.ka(c) * (A - (R)prm.a0(c));
+            cc.y = (R)2 * (R)prm.kp(c) * (Pp - (R)prm.p0(c));
+            cell[c] = cc;
+          }
+        }
+      }
+      return fl;
+    }
 #pragma unroll
     for (int k = 0; k < MAXC; ++k) {
       const int c = f0 + k * st;
@@ -902,15 +928,35 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
   const R lminR = (R)mp.l_min;
   double dt = mp.dt0, alpha = mp.alpha0, fmx = 0;
   int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
+  auto cell_coef = [&](int c, R A, R Pp) {
+    R2 cc;
+    cc.x = (R)(2.0 * prm.ka(c)) * (A - (R)prm.a0(c));
+    cc.y = (R)(2.0 * prm.kp(c)) * (Pp - (R)prm.p0(c));
+    cell[c] = cc;
+  };
   auto cell_pass = [&](R lm) -> bool {
     bool fl = false;
+    if (vw.ccor) {
+      // two cells per thread with both gathers in flight (flat tables)
+      for (int c0 = tid; c0 < n; c0 += 2 * T) {
+        const int c1 = c0 + T;
+        CGather<P> g0, g1;
+        cell_gather(vw, c0, g0);
+        if (c1 < n) cell_gather(vw, c1, g1);
+        R A, Pp;
+        fl |= cell_geometry_g(vw, c0, g0, A, Pp, lm, shortbits);
+        cell_coef(c0, A, Pp);
+        if (c1 < n) {
+          fl |= cell_geometry_g(vw, c1, g1, A, Pp, lm, shortbits);
+          cell_coef(c1, A, Pp);
+        }
+      }
+      return fl;
+    }
     for (int c = tid; c < n; c += T) {
       R A, Pp;
       fl |= cell_geometry(vw, c, A, Pp, lm, shortbits);
-      R2 cc;
-      cc.x = (R)(2.0 * prm.ka(c)) * (A - (R)prm.a0(c));
-      cc.y = (R)(2.0 * prm.kp(c)) * (Pp - (R)prm.p0(c));
-      cell[c] = cc;
+      cell_coef(c, A, Pp);
     }
     return fl;
   };
@@ -958,9 +1004,7 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
       aniso_nudge_pass(vw, tid, T, mp.aniso_ws, G[0], G[1], G[2], (double2*)mp.aniso_nudge);
     }
     double red[4] = {0, 0, 0, 0};
-    for (int i = tid; i < V; i += T) {
-      R fx, fy;
-      vertex_force(vw, i, cell, lam, prm.lam_s, fx, fy);
+    auto vertex_tail = [&](int i, R fx, R fy) {
       if (nudged_v2v) {
         double gx, gy;
         v2v_grad(vw, i, mp.cost_data, gx, gy);
@@ -982,6 +1026,20 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
       red[1] += (double)(fx * u.x + fy * u.y);
       red[2] += (double)(u.x * u.x + u.y * u.y);
       red[3] = fmax(red[3], f2);
+    };
+    // two vertices per thread with both gathers in flight
+    for (int i0 = tid; i0 < V; i0 += 2 * T) {
+      const int i1 = i0 + T;
+      VGather<P> g0, g1;
+      vertex_gather(vw, i0, cell, lam, prm.lam_s, g0);
+      if (i1 < V) vertex_gather(vw, i1, cell, lam, prm.lam_s, g1);
+      R fx, fy;
+      vertex_compute(vw, g0, fx, fy);
+      vertex_tail(i0, fx, fy);
+      if (i1 < V) {
+        vertex_compute(vw, g1, fx, fy);
+        vertex_tail(i1, fx, fy);
+      }
     }
     tm.template reduce<4>(red, sl.a, 1);
     fmx = sqrt(red[3]);

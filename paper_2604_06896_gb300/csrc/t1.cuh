@@ -180,7 +180,7 @@ __device__ __noinline__ bool t1_evaluate(const View<P>& v, const ParamsD& prm, d
   const int s1 = __shfl_sync(0xffffffffu, fs, 0), s2 = __shfl_sync(0xffffffffu, fs, 1);
   const int s3 = __shfl_sync(0xffffffffu, fs, 2), s4 = __shfl_sync(0xffffffffu, fs, 3);
   const int* C = k.C;
-  k.allow = s1 > 3 && s2 > 3 && (!v.ccor || (s3 < kMaxCorners && s4 < kMaxCorners)) &&
+  k.allow = s1 > 3 && s2 > 3 && s3 < kMaxCorners && s4 < kMaxCorners &&
             C[0] != C[1] && C[0] != C[2] &&
             C[0] != C[3] && C[1] != C[2] && C[1] != C[3] && C[2] != C[3] && k.kyx >= -1 &&
             k.kyx <= 1 && k.kyy >= -1 && k.kyy <= 1 && k.kzx >= -1 && k.kzx <= 1 && k.kzy >= -1 &&

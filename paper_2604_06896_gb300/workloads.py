@@ -23,16 +23,23 @@ import math
 import numpy as np
 
 
-def rigidity_sweep(vx, seeds_list, box, p0_grid, energy_threshold=1e-8, dtype="f64",
-                   opts=None):
+def rigidity_sweep(vx, seeds_list, box, p0_grid, energy_threshold=1e-6, dtype="f64",
+                   opts=None, return_states=False):
     """Relax every tissue at every p0 of p0_grid in one batched launch.
 
     seeds_list: list of seed arrays (one tissue each) in a box (Lx, Ly) of
     area n A0 with A0 = 1; the energy is the dimensionless E1 of Eq.
-    (Energy1) (K_A = K_P = 1, no line tension).  A relaxation is a
-    zero-energy state when its final energy per cell is below
-    energy_threshold.  Returns dict(p0, fraction, energies [len(p0), tissues],
-    fit=(p_star, width), results)."""
+    (Energy1) (K_A = K_P = 1, no line tension); FIRE with the T1 rule of
+    Methods, "T1 transitions" (l_min = 5e-3).  A relaxation is a zero-energy
+    state when its final energy per cell is below energy_threshold.  The
+    default 1e-6 separates the two populations the relaxations end in: the
+    floppy states keep meeting short edges (stretches and T1s, each a
+    perturbation of order K_P l_min^2 = 2.5e-5 on a cell) and end between
+    1e-11 and 1e-6 per cell, the rigid minima at 6e-6 per cell and above
+    next to the transition.  Returns dict(p0, fraction, energies
+    [len(p0), tissues], fit=(p_star, width), results) and, with
+    return_states, the relaxed positions and topologies (tissue-major, p0
+    minor: entry t * len(p0_grid) + j)."""
     import torch
     Lx, Ly = box
     meshes = [vx.vx_build_mesh(s, Lx, Ly) for s in seeds_list]
@@ -45,13 +52,19 @@ def rigidity_sweep(vx, seeds_list, box, p0_grid, energy_threshold=1e-8, dtype="f
     o = dict(tol=1e-10, max_iter=50000, dt0=0.01, dt_max=0.5, l_min=5e-3)
     o.update(opts or {})
     rs = vx.vx_minimize_batched(b, X, params, **o)
+    states = None
+    if return_states:
+        states = (b.split(X.cpu().numpy()), b.topologies())
     b.close()
     n = np.array([m["face_he"].shape[0] for m in meshes for _ in range(G)], dtype=np.float64)
     e = np.array([r.energy for r in rs]) / n
     energies = e.reshape(T, G).T
     frac = (energies < energy_threshold).mean(axis=1)
-    return dict(p0=np.asarray(p0_grid, dtype=np.float64), fraction=frac, energies=energies,
-                fit=fit_sigmoid(np.asarray(p0_grid, dtype=np.float64), frac), results=rs)
+    out = dict(p0=np.asarray(p0_grid, dtype=np.float64), fraction=frac, energies=energies,
+               fit=fit_sigmoid(np.asarray(p0_grid, dtype=np.float64), frac), results=rs)
+    if states is not None:
+        out["X"], out["topologies"] = states
+    return out
 
 
 def fit_sigmoid(x, y):
