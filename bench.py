@@ -212,9 +212,10 @@ def algorithmic_bytes_per_iter(n):
 def grad_metric(vx, torch, steps, warmup):
     """Equilibrium-gradient solves/s on the 1,000-cell parameter-inference
     tissue (FP32): one solve = relax from the target equilibrium under the
-    trial tensions to max|F| < 1e-5 sqrt(A0) (FP32 arithmetic stalls near
-    1.5e-6 on this tissue), then the adjoint gradient of the v2v cost with
-    respect to the 3,000 tensions.  The persistent path (automatic choice:
+    trial tensions in FP32 to max|F| < 1e-5 sqrt(A0) (FP32 arithmetic
+    stalls near 1.5e-6 on this tissue), continue in FP64 arithmetic to
+    max|F| < 1e-8 sqrt(A0) (refine_tol), then the adjoint gradient of the
+    v2v cost with respect to the 3,000 tensions (FP32, CG to rtol 1e-6).  The persistent path (automatic choice:
     a 16-CTA cluster) against the plain path (one launch per sub-step for
     both the minimiser and the CG), same inputs and tolerances, CUDA events
     around each solve."""
@@ -234,7 +235,7 @@ def grad_metric(vx, torch, steps, warmup):
     out = {}
     for path in ("auto", "plain"):
         o = opts_for(c["A0"], path)
-        o["tol"], o["max_iter"] = 1e-5 * sA, 100_000
+        o["tol"], o["refine_tol"], o["max_iter"] = 1e-8 * sA, 1e-5 * sA, 100_000
 
         def solve():
             vx.vx_tissue_restore(t)
@@ -267,9 +268,9 @@ def grad_metric(vx, torch, steps, warmup):
                      "cg_rel_residual": rg.cg_rel_residual}
     t.close()
     return {"metric": "equilibrium-gradient solves/s", "unit": "solves/s",
-            "workload": "c4: 1,000-cell tissue, 3,000 tension parameters, v2v cost; relax to "
-                        "max|F|<1e-5*sqrt(A0) from the target equilibrium, then the adjoint "
-                        "(CG to rtol 1e-6)",
+            "workload": "c4: 1,000-cell tissue, 3,000 tension parameters, v2v cost; relax "
+                        "from the target equilibrium in FP32 to max|F|<1e-5*sqrt(A0), then in "
+                        "FP64 to 1e-8*sqrt(A0), then the FP32 adjoint (CG to rtol 1e-6)",
             "value": out["auto"]["value"], "vs_plain_gpu_path": out["auto"]["value"] / out["plain"]["value"],
             "persistent": out["auto"], "plain_gpu_path": out["plain"]}, check
 
@@ -277,7 +278,7 @@ def grad_metric(vx, torch, steps, warmup):
 def c4_oracle_errors(check):
     """The oracle at the GPU's c4 result: its dense adjoint gradient at the
     GPU's equilibrium and topology (the FP32 adjoint's error), and its
-    max |F| there (how far the FP32 equilibrium is from force balance)."""
+    max |F| there (how far the GPU's equilibrium is from force balance)."""
     from oracle import model as omodel
     from oracle import solvers as osolv
     top = dict(check["top"], vert=check["X"])
@@ -288,8 +289,8 @@ def c4_oracle_errors(check):
     return {"adjoint_rel_error": float(np.linalg.norm(d) / np.linalg.norm(g_ref["lam"])),
             "oracle_fmax_at_X": float(np.sqrt((F * F).sum(axis=1)).max()),
             "gpu_fmax": check["fmax"], "hessian_pd": bool(info["pd"]),
-            "note": "oracle dense adjoint at the GPU's FP32 equilibrium and topology; the "
-                    "end-to-end error of the FP32 pipeline against the oracle's own FP64 "
+            "note": "oracle dense adjoint at the GPU's equilibrium and topology; the "
+                    "end-to-end error of the GPU pipeline against the oracle's own FP64 "
                     "pipeline is measured by tests/test_gpu_c4.py"}
 
 

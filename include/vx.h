@@ -213,6 +213,13 @@ typedef struct {
   int32_t* edge_events;/* dev int32 [E][2] or NULL: per edge, the number of
                           stretches ([e][0]) and T1s ([e][1]) the T1 passes
                           made are added (a diagnostic of repeated events) */
+  double  refine_tol;  /* FP32 tissues, vx_minimize only: when > tol, the
+                          solve runs in FP32 arithmetic until max|F| <
+                          refine_tol, then continues from there in FP64
+                          arithmetic to tol (FP32 forces carry ~3e-7
+                          relative rounding, below which FP32 FIRE stalls);
+                          the iteration budget is shared; 0 (default): one
+                          precision throughout                             */
 } vx_min_opts;
 
 typedef struct {
@@ -275,10 +282,12 @@ typedef struct {
   const double* cost_data; /* dev: X_target [V][2] (v2v) or q_target [2]     */
   vx_min_opts inner;   /* nudged phases (T1 is not applied in them, nor the
                           exit-time wrap)                                   */
-  int32_t ep_f64;      /* EP on an FP32 tissue: 1 runs the nudged phases in
-                          FP64 arithmetic (the estimate divides a difference
-                          of two equilibria by beta, so their force balance
-                          must be finer than FP32 forces allow); default 0 */
+  int32_t ep_f64;      /* EP on an FP32 tissue: 1 (default) runs the nudged
+                          phases in FP64 arithmetic (the estimate divides a
+                          difference of two equilibria by beta, so their
+                          force balance must be finer than FP32 forces
+                          allow); 0 keeps them in FP32 (about 4e-2 relative
+                          error against the FP64 estimate at beta = 1e-2) */
 } vx_grad_opts;
 
 typedef struct {

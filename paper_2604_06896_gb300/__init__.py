@@ -275,7 +275,7 @@ def vx_minimize_async(t: Tissue, X, params, result, **opts):
 
 def vx_equilibrium_grad_async(t: Tissue, Xstar, params, g, result, dCdX=None, mode=VX_ADJOINT_CG,
                               beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, cost=VX_COST_NONE,
-                              cost_data=None, inner=None, ep_f64=0):
+                              cost_data=None, inner=None, ep_f64=1):
     """vx_equilibrium_grad without host synchronisation (see vx.h): the
     gradients go to the device tensors g["lam"], g["A0"], g["P0"] (each may
     be missing) and the GPU writes the result into `result` (a
@@ -336,7 +336,7 @@ class GradResult:
 
 def vx_equilibrium_grad(t: Tissue, Xstar, params, dCdX=None, mode=VX_ADJOINT_CG, beta=1e-3,
                         cg_rtol=1e-10, cg_max_iter=20000, cost=VX_COST_NONE, cost_data=None,
-                        inner=None, ep_f64=0):
+                        inner=None, ep_f64=1):
     """Gradient of the outer cost at the equilibrium X* with respect to
     (Lambda, A0, P0).  Returns (dict of device f64 tensors, GradResult)."""
     torch = _torch()
@@ -577,7 +577,7 @@ def vx_equilibrium_grad_batched(b: Batch, Xstar, params, dCdX, cg_rtol=1e-10, cg
 
 
 def vx_batch_grad(b: Batch, X, params, cost, cost_data, what=3, free=None, mode=VX_EP_CENTERED,
-                  beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, inner=None, ep_f64=0,
+                  beta=1e-3, cg_rtol=1e-10, cg_max_iter=20000, inner=None, ep_f64=1,
                   strict=True):
     """The batched gradient workload in one launch (see vx.h): relax every
     tissue (X: device f64 [sum V, 2], updated in place to X*), then the

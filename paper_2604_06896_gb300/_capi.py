@@ -50,7 +50,7 @@ class vx_min_opts(C.Structure):
                 ("dt_max", C.c_double), ("n_min", C.c_int32), ("f_inc", C.c_double),
                 ("f_dec", C.c_double), ("alpha0", C.c_double), ("f_alpha", C.c_double),
                 ("l_min", C.c_double), ("path", C.c_int32), ("check_every", C.c_int32),
-                ("wrap", C.c_int32), ("edge_events", C.c_void_p)]
+                ("wrap", C.c_int32), ("edge_events", C.c_void_p), ("refine_tol", C.c_double)]
 
 
 class vx_min_result(C.Structure):

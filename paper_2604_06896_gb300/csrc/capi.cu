@@ -389,6 +389,7 @@ void vx_min_opts_default(vx_min_opts* o) {
   o->check_every = 50;
   o->wrap = 1;
   o->edge_events = nullptr;
+  o->refine_tol = 0.0;
 }
 
 static bool min_opts_ok(const vx_min_opts* o, std::string* m) {
@@ -434,9 +435,43 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
   if (!params_ok(p, &m) || !min_opts_ok(o, &m)) return invalid(m);
   vx::MinOut out = {};
   int used = 0;
-  const vx_status s = vx::minimize(t, X, to_params(p), to_min_params(o), o->path, o->check_every,
-                                   &out, &used, as_stream(stream));
+  const vx::ParamsD prm = to_params(p);
+  vx::MinParams mp = to_min_params(o);
+  const bool refine = t->dtype == VX_F32 && o->refine_tol > o->tol;
+  if (refine) {
+    mp.tol = o->refine_tol;
+    mp.wrap = 0;
+  }
+  vx_status s = vx::minimize(t, X, prm, mp, o->path, o->check_every, &out, &used,
+                             as_stream(stream));
   if (s != VX_OK) return s;
+  if (refine && out.status == VX_OK && out.iters < o->max_iter) {
+    // FP64 arithmetic from the FP32 result (X is FP64 in and out; the
+    // tissue's buffers hold either precision)
+    const vx::MinOut first = out;
+    vx::MinParams mp2 = to_min_params(o);
+    mp2.max_iter = o->max_iter - first.iters;
+    const int saved = t->dtype;
+    t->dtype = VX_F64;
+    out = vx::MinOut{};
+    s = vx::minimize(t, X, prm, mp2, o->path, o->check_every, &out, &used, as_stream(stream));
+    t->dtype = saved;
+    if (s != VX_OK) return s;
+    out.iters += first.iters;
+    out.n_t1 += first.n_t1;
+    out.n_stretch += first.n_stretch;
+    out.force_evals += first.force_evals;
+  } else if (refine && o->wrap) {
+    vx::MinParams mw = to_min_params(o);
+    mw.max_iter = 0;    // no step and no T1 check: the exit-time wrap only
+    mw.l_min = 0.0;
+    const vx::MinOut first = out;
+    s = vx::minimize(t, X, prm, mw, o->path, o->check_every, &out, &used, as_stream(stream));
+    if (s != VX_OK) return s;
+    const int wrap_err = out.wrap_err;
+    out = first;
+    out.wrap_err = wrap_err;
+  }
   r->status = out.status;
   r->iters = out.iters;
   r->n_t1 = out.n_t1;
@@ -502,6 +537,7 @@ void vx_grad_opts_default(vx_grad_opts* o) {
   o->cost_data = nullptr;
   vx_min_opts_default(&o->inner);
   o->inner.tol = 1e-10;
+  o->ep_f64 = 1;
 }
 
 }  // extern "C"

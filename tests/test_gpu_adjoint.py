@@ -96,7 +96,8 @@ def test_ep_vs_oracle_and_adjoint(vx, equilibrium, dtype, ep_f64):
     ~ (FP32 force noise) / (softest Hessian eigenvalue) along the soft
     modes, by beta: FP32 forces carry ~3e-7 relative noise, the phases stop
     at 2e-6, beta = 1 keeps the quotient small, and the error is a few
-    per cent (the bound below; the measured value is printed)."""
+    per cent (3.6e-2 measured against the oracle's EP; the bound below).
+    EP on FP32 tissues therefore runs its nudged phases in FP64 by default."""
     c, t, p, X, Xt = equilibrium
     gradC = lambda Y: omodel.cost_v2v(Y, Xt, t)[1]
     g_adj, _, _ = osolv.adjoint_grad(X, t, p, gradC(X))
@@ -115,8 +116,8 @@ def test_ep_vs_oracle_and_adjoint(vx, equilibrium, dtype, ep_f64):
     assert r.status == 0
     C, _ = omodel.cost_v2v(X, Xt, t)
     assert abs(r.cost - C) < 1e-10 * C
-    assert e_ref < (1e-1 if fp32_phases else 1e-7)
-    assert e_adj < (1e-1 if fp32_phases else 1e-4)
+    assert e_ref < (5e-2 if fp32_phases else 1e-7)
+    assert e_adj < (5e-2 if fp32_phases else 1e-4)
     tis.close()
 
 

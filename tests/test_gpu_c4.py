@@ -131,18 +131,19 @@ def test_c4_fp32_pipeline_vs_oracle(vx, c4_oracle):
     are printed and bounded.  The gradient error is set by the relaxation
     tolerance: an equilibrium known to max|F| ~ tol is off by ~ tol /
     lambda_min along the softest mode, and the v2v gradient is linear in
-    X* - X_target (the errors at the benchmark's tolerance and at the FP32
-    floor are both reported)."""
+    X* - X_target (the errors at 1e-5, at the FP32 floor 2e-6, and with the
+    FP64 refinement to 1e-8 that the benchmark uses are all reported; the
+    refined pipeline meets the 1e-4 bounds on positions and gradients)."""
     import torch
     c, base, tgt, top_ref, g_ref, C_ref = c4_oracle
     p = dict(base, lam=c["lam"])
     Xt = torch.tensor(tgt["vert"], dtype=torch.float64, device="cuda")
     out = {}
-    for tol in (1e-5, 2e-6):
+    for tol, refine in ((1e-5, 0.0), (2e-6, 0.0), (1e-8, 1e-5)):
         t = vx.Tissue(tgt, "f32")
         X = Xt.clone()
         r = vx.vx_minimize(t, X, p, tol=tol, max_iter=100000, dt0=0.01, dt_max=0.5, l_min=5e-3,
-                           path="cluster", wrap=0)
+                           path="cluster", wrap=0, refine_tol=refine)
         top = t.topology()
         g, rg = vx.vx_equilibrium_grad(t, X, p, cost=vx.VX_COST_V2V, cost_data=Xt, cg_rtol=1e-6)
         ex = np.abs(X.cpu().numpy() - top_ref["vert"]).max()
@@ -155,3 +156,4 @@ def test_c4_fp32_pipeline_vs_oracle(vx, c4_oracle):
         t.close()
     assert out[1e-5][1] < 5e-2
     assert out[2e-6][1] < 1e-2
+    assert out[1e-8][0] < 1e-4 and out[1e-8][1] < 1e-4
