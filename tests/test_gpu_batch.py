@@ -28,7 +28,27 @@ def tissues(sizes, stream0, p0s):
     return out
 
 
+def soft_mode_bound(X, top, p, tol):
+    """How far two relaxations that both stopped at max_i |F_i| < tol can
+    end apart: each is within |F|_2 / lambda_min < tol sqrt(V) / lambda_min
+    of the exact minimum (lambda_min: the smallest eigenvalue of the
+    oracle's Hessian off the two rigid translations), so twice that."""
+    H = omodel.hessian(X, top, p, dense=True)
+    w = np.sort(np.linalg.eigvalsh(H))
+    assert w[2] > 0
+    return 2.0 * tol * np.sqrt(X.shape[0]) / w[2], w[2]
+
+
 def test_batch_fp64_matches_oracle(vx):
+    """FP64 batched relaxations (FIRE + T1) against the oracle: the same T1
+    decisions and final topology, the same energy, and positions within the
+    soft-mode bound.  The trajectories agree up to rounding order; over a
+    long relaxation along soft modes a FIRE control decision (the sign of
+    F.v near zero) eventually falls the other way, after which the two runs
+    take different step sequences to the same minimum: the iteration counts
+    then differ by a few per cent and the end points by up to
+    tol sqrt(V) / lambda_min.  The single-tissue resident path on the same
+    inputs shows the same drift (printed beside the batch's)."""
     import torch
     sizes = [30, 120, 45, 80, 200, 60, 150, 35]
     p0s = [3.6 + 0.03 * k for k in range(len(sizes))]
@@ -37,24 +57,30 @@ def test_batch_fp64_matches_oracle(vx):
     X = torch.tensor(np.concatenate([m["vert"] for _, m in ts]), dtype=torch.float64, device="cuda")
     lam = np.concatenate([c["lam"] for c, _ in ts])
     params = dict(KA=1.0, KP=1.0, A0=1.0, P0=np.array(p0s), lam=torch.tensor(lam, device="cuda"))
-    rs = vx.vx_minimize_batched(b, X, params, tol=1e-9, max_iter=50000, dt0=0.01, dt_max=0.5,
-                                l_min=5e-3, wrap=0)
+    kw = dict(tol=1e-9, max_iter=50000, dt0=0.01, dt_max=0.5, l_min=5e-3, wrap=0)
+    rs = vx.vx_minimize_batched(b, X, params, **kw)
     tops = b.topologies()
     Xs = b.split(X.cpu().numpy())
     for k, ((c, m), r) in enumerate(zip(ts, rs)):
         p = dict(KA=1.0, KP=1.0, A0=1.0, P0=p0s[k], lam=c["lam"])
         ro = osolv.relax(m["vert"], m, p, osolv.MinOpts(tol=1e-9, max_iter=50000, dt0=0.01,
                                                         dt_max=0.5), l_min=5e-3)
-        print(f"tissue {k} n={sizes[k]}: gpu {r.iters} it {r.n_t1} T1; oracle {ro.iters} it {ro.n_t1} T1")
+        t = vx.Tissue(m, "f64")
+        Xk = torch.tensor(m["vert"], dtype=torch.float64, device="cuda")
+        r1 = vx.vx_minimize(t, Xk, p, path="resident", **kw)
+        t.close()
+        bound, lmin = soft_mode_bound(ro.X, ro.tissue, p, 1e-9)
+        d = np.abs(Xs[k] - ro.X).max()
+        d1 = np.abs(Xk.cpu().numpy() - ro.X).max()
+        print(f"tissue {k} n={sizes[k]}: batch {r.iters} it, single {r1.iters} it, oracle "
+              f"{ro.iters} it ({r.n_t1} T1); |X - X_oracle| batch {d:.1e} single {d1:.1e}, "
+              f"bound {bound:.1e} (lambda_min {lmin:.1e})")
         assert r.converged and ro.converged
         assert (r.n_t1, r.n_stretch) == (ro.n_t1, ro.n_stretch)
         assert np.array_equal(tops[k]["he"], ro.tissue["he"])
-        # the same trajectory up to rounding order; long soft relaxations may
-        # drift apart by a few per cent in iterations, ending at the same
-        # equilibrium (energy) within the soft-mode tolerance
         assert abs(r.iters - ro.iters) <= max(2, 0.05 * ro.iters)
         assert abs(r.energy - omodel.energy(ro.X, ro.tissue, p)) < 1e-9 * abs(r.energy)
-        assert np.abs(Xs[k] - ro.X).max() < 1e-4
+        assert d < bound
     b.close()
 
 
