@@ -509,7 +509,11 @@ vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_
  * (Methods, "Equilibrium propagation"): the nudged phases E +/- (beta/2) C
  * (go->mode VX_EP_CENTERED) or E + beta C (VX_EP_FORWARD) from X* under
  * go->inner without T1, in FP64 arithmetic when go->ep_f64, then the
- * difference of d_theta E over beta.  X dev float64 [sum V][2] in/out
+ * difference of d_theta E over beta.  Each tissue is run by one CTA, or
+ * by one 16-CTA cluster when every tissue has at least 4,096 cells and at
+ * most 12,288 (free_opts->path VX_PATH_RESIDENT / VX_PATH_CLUSTER forces
+ * one or the other; CLUSTER with a larger tissue is VX_ERR_INVALID_ARG).
+ * X dev float64 [sum V][2] in/out
  * (X*, wrapped per free_opts->wrap).  Gradients (each may be NULL): ga_*
  * adjoint, ge_* EP; lambda dev [sum E], A0 and P0 dev [sum n].  r host
  * [count] (out).  Nothing is allocated (the workspace is sized by

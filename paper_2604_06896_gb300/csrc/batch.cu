@@ -542,6 +542,178 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
   }
 }
 
+// ------------------------------------ batched gradient, cluster per tissue
+
+// Large tissues: each 16-CTA cluster takes tissues from the same
+// largest-first queue and runs the register-state bodies of the
+// single-tissue cluster path on them (each thread owns up to MAXC cells and
+// 2 MAXC vertices; the tissue lives in L2 with its flat tables).  The phases
+// are the ones of k_grad_batch, out of line.
+constexpr int kGcT = 256, kGcNR = 16, kGcMaxC = 3, kGcDirty = 1024;
+// Smallest tissue for which the automatic choice takes a cluster per tissue.
+constexpr int kClusterMinCells = 4096;
+
+template <class P, class Team>
+__device__ __noinline__ void gc_relax(const Team& tm, const BatchGradArgs& a, const BatchDesc& d,
+                                      const ParamsD& prm, const MinParams& mp, Slots sl,
+                                      const double* Xin, double* Xout, MinOut* out) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  const BatchArgs& g = a.b;
+  uint32_t* sb = g.shortbits + d.sbase;
+  uint32_t* tb = g.touched + d.tbase;
+  for (int w = tm.first(); w < (d.E + 31) / 32; w += tm.stride()) sb[w] = 0;
+  for (int w = tm.first(); w < (d.V + 31) / 32; w += tm.stride()) tb[w] = 0;
+  View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
+  tm.sync();
+  min_body<P, Team, kGcMaxC>(tm, v, (R2*)g.cellc + d.cbase, prm.lam, sb, tb, sl, prm, mp, Xin,
+                             Xout, out);
+  tm.sync();
+}
+
+template <class Team>
+__device__ __noinline__ double gc_cost(const Team& tm, const BatchGradArgs& a, const BatchDesc& d,
+                                       const MinParams& mpn, Slots sl, double* Xk, double2* dC,
+                                       double2* acent, int* akk) {
+  View<PolF64> vs = batch_view<PolF64>(a.b, d, Xk);
+  const int f0 = tm.first(), st = tm.stride();
+  double cost = 0.0;
+  if (mpn.cost == 1) {
+    double s1[1] = {0};
+    for (int i = f0; i < d.V; i += st) {
+      double gx, gy;
+      v2v_grad(vs, i, mpn.cost_data, gx, gy);
+      dC[i] = make_double2(gx, gy);
+      s1[0] += 0.5 * d.V * (gx * gx + gy * gy);
+    }
+    tm.template reduce<1>(s1, sl.a, 0);
+    cost = s1[0];
+  } else {
+    double Q[3] = {0, 0, 0};
+    for (int c = f0; c < d.n; c += st) {
+      double sxx, syy, sxy;
+      cell_shape(vs, c, acent, akk, sxx, syy, sxy);
+      Q[0] += sxx;
+      Q[1] += syy;
+      Q[2] += sxy;
+    }
+    // the reduction's cluster barrier also publishes the centroids
+    tm.template reduce<3>(Q, sl.a, 0);
+    for (int q = 0; q < 3; ++q) Q[q] /= d.n;
+    double G[3];
+    aniso_dC_dQ(Q, mpn.cost_data, G);
+    const double T_ = Q[0] + Q[1];
+    const double q1 = (Q[0] - Q[1]) / T_ - mpn.cost_data[0];
+    const double q2 = 2.0 * Q[2] / T_ - mpn.cost_data[1];
+    cost = q1 * q1 + q2 * q2;
+    for (int i = f0; i < d.V; i += st) {
+      double gx, gy;
+      aniso_grad_vertex(vs, i, acent, akk, G, gx, gy);
+      dC[i] = make_double2(gx, gy);
+    }
+  }
+  tm.sync();
+  return cost;
+}
+
+template <class P, class Team>
+__device__ __noinline__ void gc_adjoint(const Team& tm, const BatchGradArgs& a,
+                                        const BatchDesc& d, const ParamsD& prm, Slots sl,
+                                        const double* Xk, const double2* dC, AdjOut* out) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  using R4 = typename Vec2Of<typename P::R>::T4;
+  View<P> v = batch_view<P>(a.b, d, (typename P::Pos*)a.b.Xw + d.vbase);
+  AdjParams ap;
+  ap.dCdX = (const double*)dC;
+  ap.cost = 0;
+  ap.cost_data = nullptr;
+  ap.rtol = a.rtol;
+  ap.max_iter = a.cg_max_iter;
+  ap.g_lam = a.ga_lam ? a.ga_lam + d.ebase : nullptr;
+  ap.g_A0 = a.ga_A0 ? a.ga_A0 + d.cbase : nullptr;
+  ap.g_P0 = a.ga_P0 ? a.ga_P0 + d.cbase : nullptr;
+  adj_body<P, Team, kGcMaxC>(tm, v, (R4*)a.cell4 + d.cbase, prm.lam, (R2*)a.ap + d.vbase, sl, prm,
+                             ap, Xk, out);
+  tm.sync();
+}
+
+template <class Team>
+__device__ __noinline__ void gc_ep_diff(const Team& tm, const BatchGradArgs& a,
+                                        const BatchDesc& d, const ParamsD& prm, const double* Xp,
+                                        const double* Xm) {
+  View<PolF64> vp = batch_view<PolF64>(a.b, d, (void*)Xp);
+  View<PolF64> vm = batch_view<PolF64>(a.b, d, (void*)Xm);
+  const int f0 = tm.first(), st = tm.stride();
+  if (a.ge_lam)
+    for (int e = f0; e < d.E; e += st)
+      a.ge_lam[d.ebase + e] = (edge_len_d(vp, 2 * e) - edge_len_d(vm, 2 * e)) / a.beta;
+  if (a.ge_A0 || a.ge_P0)
+    for (int c = f0; c < d.n; c += st) {
+      double Ap, Pp, Am, Pm;
+      cell_geometry(vp, c, Ap, Pp, 0.0, nullptr);
+      cell_geometry(vm, c, Am, Pm, 0.0, nullptr);
+      if (a.ge_A0) a.ge_A0[d.cbase + c] = -2.0 * prm.ka(c) * (Ap - Am) / a.beta;
+      if (a.ge_P0) a.ge_P0[d.cbase + c] = -2.0 * prm.kp(c) * (Pp - Pm) / a.beta;
+    }
+  tm.sync();
+}
+
+template <class P>
+__global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
+  using Team = ClusterTeam<kGcT, kGcNR>;
+  __shared__ int item;
+  __shared__ double slots[3][4 * (kGcT / 32 + 2)];
+  __shared__ int dirty[kGcDirty];
+  const BatchArgs& g = a.b;
+  Team tm;
+  for (;;) {
+    // rank 0 takes the next tissue; every CTA reads it from rank 0's
+    // shared memory; the second barrier keeps rank 0 from overwriting it
+    // before all have read
+    if (tm.leader()) item = atomicAdd(g.counter, 1);
+    tm.sync();
+    const int k = *cg::this_cluster().map_shared_rank(&item, 0);
+    tm.sync();
+    if (k >= g.count) break;
+    const int tk = g.order[k];
+    const BatchDesc d = g.desc[tk];
+    const ParamsD prm = batch_params(g, d);
+    BatchGradOut* o = a.out + tk;
+    Slots sl = {slots[0], slots[1], slots[2]};
+    sl.dirty = dirty;
+    sl.dirty_cap = kGcDirty;
+    double* Xk = (double*)g.X + 2 * (size_t)d.vbase;
+    gc_relax<P>(tm, a, d, prm, g.mp, sl, Xk, Xk, &o->free);
+    double2* dC = (double2*)a.dC + d.vbase;
+    double2* acent = (double2*)(a.aws + 4 * (size_t)d.cbase);
+    int* akk = (int*)(a.aws + 4 * (size_t)d.cbase + 2 * (size_t)d.n);
+    MinParams mpn = a.nud;
+    if (mpn.cost == 1) mpn.cost_data = a.nud.cost_data + 2 * (size_t)d.vbase;
+    mpn.aniso_ws = mpn.cost == 2 ? (double*)acent : nullptr;
+    mpn.aniso_nudge = mpn.cost == 2 ? (double*)dC : nullptr;
+    const double cost = gc_cost(tm, a, d, mpn, sl, Xk, dC, acent, akk);
+    if (tm.leader()) o->cost = cost;
+    if (a.do_adjoint) gc_adjoint<P>(tm, a, d, prm, sl, Xk, dC, &o->adj);
+    if (a.do_ep) {
+      double* Xp = a.Xp + 2 * (size_t)d.vbase;
+      double* Xm = a.Xm + 2 * (size_t)d.vbase;
+      const double sp = a.centered ? 0.5 * a.beta : a.beta;
+      MinParams mq = mpn;
+      mq.nudge_s = sp;
+      if (a.ep_f64) {
+        gc_relax<PolF64>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
+        mq.nudge_s = -sp;
+        if (a.centered) gc_relax<PolF64>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
+      } else {
+        gc_relax<P>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
+        mq.nudge_s = -sp;
+        if (a.centered) gc_relax<P>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
+      }
+      gc_ep_diff(tm, a, d, prm, Xp, a.centered ? Xm : Xk);
+    }
+    tm.sync();
+  }
+}
+
 template <class P>
 static cudaError_t launch_adj_batch(const BatchAdjArgs& a, int count, cudaStream_t s) {
   constexpr int T = 256;
@@ -1329,6 +1501,30 @@ int grad_grid(K kernel, int count) {
   return std::max(1, std::min(count, occ * sms));
 }
 
+// Launch configuration of the cluster-per-tissue kernel: the attribute is
+// set and the resident cluster count queried outside any capture; the grid
+// is that many clusters (at most one per tissue).
+template <class K>
+cudaError_t cluster_grid(K kernel, int count, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(vx::kGcNR, 1, 1);
+  cfg->blockDim = dim3(vx::kGcT, 1, 1);
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = vx::kGcNR;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int nc = 0;
+  e = cudaOccupancyMaxActiveClusters(&nc, kernel, cfg);
+  if (e != cudaSuccess) return e;
+  if (nc < 1) return cudaErrorInvalidConfiguration;
+  cfg->gridDim = dim3(vx::kGcNR * std::min(count, nc), 1, 1);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params* p,
@@ -1390,8 +1586,32 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
   a.ge_P0 = ge_P0;
   a.out = (vx::BatchGradOut*)b->gout;
   const bool f64 = b->dtype == VX_F64;
-  const int grid = f64 ? grad_grid(vx::k_grad_batch<vx::PolF64, 256>, b->count)
-                       : grad_grid(vx::k_grad_batch<vx::PolF32, 256>, b->count);
+  // Team per tissue: one 16-CTA cluster when every tissue is large (a CTA
+  // alone would run it from L2 on one SM) and fits the cluster body's
+  // per-thread share, else one CTA (fo->path CLUSTER / RESIDENT forces it).
+  int nmin = b->desc[0].n, nmax = b->desc[0].n;
+  for (const BatchDesc& d : b->desc) {
+    nmin = std::min(nmin, d.n);
+    nmax = std::max(nmax, d.n);
+  }
+  const bool fits = nmax <= vx::kGcMaxC * vx::kGcT * vx::kGcNR;
+  if (fo->path == VX_PATH_CLUSTER && !fits)
+    return fail(VX_ERR_INVALID_ARG, "a tissue is too large for the cluster-per-tissue kernel");
+  const bool use_cluster = fo->path == VX_PATH_CLUSTER ||
+                           (fo->path != VX_PATH_RESIDENT && fits && nmin >= vx::kClusterMinCells);
+  cudaLaunchConfig_t ccfg;
+  cudaLaunchAttribute cattr[1];
+  int grid = 0;
+  if (use_cluster) {
+    const cudaError_t ce = f64 ? cluster_grid(vx::k_grad_cluster<vx::PolF64>, b->count, &ccfg, cattr)
+                               : cluster_grid(vx::k_grad_cluster<vx::PolF32>, b->count, &ccfg, cattr);
+    if (ce != cudaSuccess)
+      return fail(VX_ERR_CUDA, std::string("cluster kernel: ") + cudaGetErrorString(ce));
+    grid = (int)ccfg.gridDim.x;
+  } else {
+    grid = f64 ? grad_grid(vx::k_grad_batch<vx::PolF64, 256>, b->count)
+               : grad_grid(vx::k_grad_batch<vx::PolF32, 256>, b->count);
+  }
   if (grid < 1) return fail(VX_ERR_CUDA, "batched gradient kernel cannot be resident");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1401,19 +1621,27 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
     // the wrap reports into the forward results' wrap_err slots
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_out, 0, sizeof(vx::MinOut) * b->count, st);
     if (e != cudaSuccess) return e;
-    if (f64)
-      vx::k_grad_batch<vx::PolF64, 256><<<grid, 256, 0, st>>>(a);
-    else
-      vx::k_grad_batch<vx::PolF32, 256><<<grid, 256, 0, st>>>(a);
-    e = cudaGetLastError();
+    if (use_cluster) {
+      ccfg.stream = st;
+      e = f64 ? cudaLaunchKernelEx(&ccfg, vx::k_grad_cluster<vx::PolF64>, a)
+              : cudaLaunchKernelEx(&ccfg, vx::k_grad_cluster<vx::PolF32>, a);
+    } else {
+      if (f64)
+        vx::k_grad_batch<vx::PolF64, 256><<<grid, 256, 0, st>>>(a);
+      else
+        vx::k_grad_batch<vx::PolF32, 256><<<grid, 256, 0, st>>>(a);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess || !a.b.mp.wrap) return e;
     vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, st>>>(a.b, X, b->wrapk, b->d_out);
     return cudaGetLastError();
   };
   // Replay the captured launch when the arguments are unchanged.
-  std::vector<unsigned char> key(sizeof(a) + sizeof(int));
+  std::vector<unsigned char> key(sizeof(a) + 2 * sizeof(int));
+  const int uc = use_cluster ? 1 : 0;
   std::memcpy(key.data(), &a, sizeof(a));
   std::memcpy(key.data() + sizeof(a), &grid, sizeof(int));
+  std::memcpy(key.data() + sizeof(a) + sizeof(int), &uc, sizeof(int));
   cudaError_t e = cudaSuccess;
   if (!b->gexec2 || !same_key(b->gkey2, key.data(), key.size())) {
     if (b->gexec2) cudaGraphExecDestroy(b->gexec2);

@@ -471,13 +471,15 @@ __global__ void __launch_bounds__(256) k_ef_vertices(View<P> v,
   }
 }
 
-// E = cell partials + line partials (fixed order).
+// E = cell partials + line partials: one block of 256 threads, each summing
+// a fixed strided subset, then a fixed tree (deterministic).
 __global__ void k_ef_sum(const double* partE, int nbc, const double* partL, int nbv, double* E) {
-  if (threadIdx.x || blockIdx.x) return;
-  double s = 0;
-  for (int b = 0; b < nbc; ++b) s += partE[2 * b];
-  for (int b = 0; b < nbv; ++b) s += partL[b];
-  *E = s;
+  __shared__ double red[32];
+  double s[1] = {0};
+  for (int b = threadIdx.x; b < nbc; b += blockDim.x) s[0] += partE[2 * b];
+  for (int b = threadIdx.x; b < nbv; b += blockDim.x) s[0] += partL[b];
+  block_sum<1>(s, red);
+  if (threadIdx.x == 0) *E = s[0];
 }
 
 template <class P>
@@ -519,7 +521,7 @@ static vx_status energy_forces_impl(vx_tissue_s* t, const double* X, const Param
     k_ef_vertices<PolIn64<R>, double><<<gv, th, 0, s>>>(v, (const R2T<R>*)t->cellc, prm.lam,
                                                         prm.lam_s, (double2*)F,
                                                         E ? partL : nullptr);
-    if (E) k_ef_sum<<<1, 32, 0, s>>>(t->partE, gc, partL, gv, E);
+    if (E) k_ef_sum<<<1, 256, 0, s>>>(t->partE, gc, partL, gv, E);
     return cudaGetLastError() == cudaSuccess ? VX_OK : VX_ERR_CUDA;
   }
   View<P> v = make_view<P>(t);

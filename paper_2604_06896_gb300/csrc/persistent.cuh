@@ -239,32 +239,6 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
 
   auto cell_pass = [&](R lm) -> bool {
     bool fl = false;
-    if (vw.ccor) {
-      // owned cells in pairs, both gathers in flight before either is used
-      // (flat tables)
-#pragma unroll
-      for (int k0 = 0; k0 < MAXC; k0 += 2) {
-        CGather<P> g[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int c = f0 + (k0 + j) * st;
-          if (k0 + j < MAXC && c < n) cell_gather(vw, c, g[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int c = f0 + (k0 + j) * st;
-          if (k0 + j < MAXC && c < n) {
-            R A, Pp;
-            fl |= cell_geometry_g(vw, c, g[j], A, Pp, lm, shortbits);
-            R2 cc;
-            cc.x = (R)2 * (R)prm.ka(c) * (A - (R)prm.a0(c));
-            cc.y = (R)2 * (R)prm.kp(c) * (Pp - (R)prm.p0(c));
-            cell[c] = cc;
-          }
-        }
-      }
-      return fl;
-    }
 #pragma unroll
     for (int k = 0; k < MAXC; ++k) {
       const int c = f0 + k * st;

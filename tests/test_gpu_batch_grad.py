@@ -148,14 +148,21 @@ def test_batch_grad_vs_oracle(vx):
     b.close()
 
 
-def test_batch_grad_c5_full_size(vx):
+@pytest.mark.parametrize("team,what", [("auto", 3), ("resident", 1)])
+def test_batch_grad_c5_full_size(vx, team, what):
     """The batched inverse-design workload at full size: 64 tissues of
     10,000 cells, FP32, anisotropy cost, per-cell A0 and per-edge tensions,
-    free relaxation (T1 on, fixed budget), adjoint and centred EP (FP64
-    nudged phases) in one launch.  Checked on sampled tissues: the oracle's
-    energy and max |F| at the returned state agree with the GPU's; the
-    batched adjoint equals the single-tissue adjoint at the same state; EP
-    and the adjoint agree to the O(beta^2) and FP32 bounds."""
+    free relaxation (T1 on, fixed budget), the adjoint and (what = 3)
+    centred EP with FP64 nudged phases, in one launch: a 16-CTA cluster per
+    tissue (the automatic choice for tissues this large) or one CTA per
+    tissue (forced).  Checked on sampled tissues: the oracle's energy, max
+    |F| and cost at the returned state agree with the GPU's, and the
+    batched adjoint equals the single-tissue adjoint at the same state.
+    EP's accuracy is not asserted here: the free relaxations stop at the
+    iteration budget with max|F| of 1e-3 to 1e-1, while the nudge
+    beta * grad C of the anisotropy cost is ~5e-8 per vertex, so the nudged
+    phases measure the continued relaxation, not the nudge (EP against the
+    adjoint at converged equilibria is asserted on smaller batches)."""
     import torch
     batch = vi.batch_c5()
     meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
@@ -165,16 +172,18 @@ def test_batch_grad_c5_full_size(vx):
     lam = torch.tensor(np.concatenate([c["lam"] for c in batch]), device="cuda")
     A0 = torch.ones(int(b.n.sum()), dtype=torch.float64, device="cuda")
     params = dict(KA=1.0, KP=1.0, A0=A0, P0=3.7, lam=lam)
-    free = dict(tol=1e-6, max_iter=10000, dt0=0.01, dt_max=0.5, l_min=5e-3)
-    inner = dict(tol=1e-7, max_iter=20000, dt0=0.01, dt_max=0.5)
-    ga, ge, rs = vx.vx_batch_grad(b, X, params, vx.VX_COST_ANISO, (0.1, 0.0), what=3, free=free,
-                                  beta=1e-2, cg_rtol=1e-6, inner=inner, ep_f64=1)
-    print("c5 free:", [r[0].status for r in rs].count(0), "converged of", b.count,
+    free = dict(tol=1e-6, max_iter=10000, dt0=0.01, dt_max=0.5, l_min=5e-3, path=team)
+    inner = dict(tol=1e-7, max_iter=5000, dt0=0.01, dt_max=0.5)
+    ga, ge, rs = vx.vx_batch_grad(b, X, params, vx.VX_COST_ANISO, (0.1, 0.0), what=what,
+                                  free=free, beta=1e-2, cg_rtol=1e-6, inner=inner, ep_f64=1)
+    print(f"c5 ({team}): free", [r[0].status for r in rs].count(0), "converged of", b.count,
           "; iters", min(r[0].iters for r in rs), max(r[0].iters for r in rs),
           "; cg", min(r[1].cg_iters for r in rs), max(r[1].cg_iters for r in rs),
           "; EP", min(r[2].nudged_iters[0] for r in rs), max(r[2].nudged_iters[0] for r in rs))
     assert all(r[0].status in (0, 1) for r in rs)
     assert all(r[1].status == 0 for r in rs)
+    if what & 2:
+        assert all(r[2].status in (0, 1) and r[2].nudged_iters[0] > 0 for r in rs)
     tops = b.topologies()
     Xs = b.split(X.cpu().numpy())
     for k in (0, 37):
@@ -193,11 +202,10 @@ def test_batch_grad_c5_full_size(vx):
                                         cost_data=np.array([0.1, 0.0]), cg_rtol=1e-6)
         t.close()
         e0, e1 = b.ebase[k], b.ebase[k] + b.E[k]
-        ga_k, ge_k = ga["lam"][e0:e1].cpu().numpy(), ge["lam"][e0:e1].cpu().numpy()
+        ga_k = ga["lam"][e0:e1].cpu().numpy()
         e_single = rel(ga_k, g1["lam"].cpu().numpy())
-        e_ep = rel(ge_k, ga_k)
+        e_ep = rel(ge["lam"][e0:e1].cpu().numpy(), ga_k) if what & 2 else float("nan")
         print(f"c5 tissue {k}: free {fr.status} {fr.iters} it fmax {fr.fmax:.1e} (oracle {fo:.1e}); "
               f"batched vs single adjoint {e_single:.1e}; EP vs adjoint {e_ep:.1e}")
         assert e_single < 1e-3
-        assert e_ep < 5e-2
     b.close()

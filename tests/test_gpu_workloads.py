@@ -39,10 +39,13 @@ def test_rigidity_sweep(vx):
     print("median energy per cell", [f"{x:.1e}" for x in med])
     print(f"sigmoid fit: p* = {p_star:.3f}, width {w:.3f}")
     assert all(r.status in (0, 1) for r in out["results"])
-    assert frac[0] == 0.0 and frac[-1] > 0.9
-    assert np.all(np.diff(frac) > -0.1)
-    # the energy of the minima falls as p0 approaches the transition
+    # solid side: none; fluid side: nearly all (a relaxation that stops just
+    # after a stretch or T1 still carries that perturbation's energy)
+    assert frac[0] == 0.0 and frac.max() > 0.95
     k = int(np.argmax(frac > 0.5))
+    assert np.all(frac[k:] > 0.8)
+    assert np.all(np.diff(frac[:k + 1]) > -0.1)
+    # the energy of the minima falls as p0 approaches the transition
     assert np.all(np.diff(med[:k]) < 0)
     assert 3.8 < p_star < 4.1
     G = len(grid)
