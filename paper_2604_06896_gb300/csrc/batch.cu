@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -67,6 +68,14 @@ struct vx_batch_s {
   double* Xtune;
   // image shifts of the exit-time wrap [V_tot]
   int2* wrapk;
+  // forward batch split between the cluster kernel (large tissues, first
+  // n_large entries of d_order2) and the CTA kernel (the rest); the side
+  // stream and events fork and join the two launches
+  int* d_order2;
+  std::vector<int> order2;
+  int n_large;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   // batched gradient workload: nudged equilibria, grad_X C at X*,
   // per-tissue anisotropy scratch, results; its own graph cache
   double *gXp, *gXm, *gdC, *gaws;
@@ -842,6 +851,47 @@ __global__ void k_wrap_batch(BatchArgs g, double* X, int2* kv, MinOut* out) {
   }
 }
 
+// Forward batch, large tissues: each 8-CTA cluster takes tissues from its
+// own largest-first queue (g.order / g.count / g.counter describe that
+// queue) and relaxes each with the register-state body of the single-tissue
+// cluster path (up to kMcMaxC cells and 2 kMcMaxC vertices per thread, the
+// tissue in L2 with its flat tables).  It runs beside k_min_batch, which
+// takes the tissues that fit shared memory, on its own share of the SMs.
+constexpr int kMcT = 256, kMcNR = 8, kMcMaxC = 3, kMcDirty = 1024;
+
+template <class P>
+__global__ void __launch_bounds__(kMcT) k_min_cluster_batch(BatchArgs g) {
+  using R2 = typename Vec2Of<typename P::R>::T;
+  using Team = ClusterTeam<kMcT, kMcNR>;
+  __shared__ int item;
+  __shared__ double slots[3][4 * (kMcT / 32 + 2)];
+  __shared__ int dirty[kMcDirty];
+  Team tm;
+  for (;;) {
+    if (tm.leader()) item = atomicAdd(g.counter, 1);
+    tm.sync();
+    const int k = *cg::this_cluster().map_shared_rank(&item, 0);
+    tm.sync();
+    if (k >= g.count) break;
+    const int tk = g.order[k];
+    const BatchDesc d = g.desc[tk];
+    const ParamsD prm = batch_params(g, d);
+    uint32_t* sb = g.shortbits + d.sbase;
+    uint32_t* tb = g.touched + d.tbase;
+    for (int w = tm.first(); w < (d.E + 31) / 32; w += tm.stride()) sb[w] = 0;
+    for (int w = tm.first(); w < (d.V + 31) / 32; w += tm.stride()) tb[w] = 0;
+    Slots sl = {slots[0], slots[1], slots[2]};
+    sl.dirty = dirty;
+    sl.dirty_cap = kMcDirty;
+    View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
+    tm.sync();
+    min_body<P, Team, kMcMaxC>(tm, v, (R2*)g.cellc + d.cbase, prm.lam, sb, tb, sl, prm, g.mp,
+                               g.X + 2 * (size_t)d.vbase, g.Xout + 2 * (size_t)d.vbase,
+                               g.out + tk);
+    tm.sync();
+  }
+}
+
 template <class P, int T>
 static cudaError_t launch_batch_t(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
   // the shared-memory attribute was set by occupancy() before any capture
@@ -1019,6 +1069,7 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   A((void**)&b->touched, 4 * (size_t)tb);
   A((void**)&b->d_out, sizeof(vx::MinOut) * count);
   A((void**)&b->wrapk, sizeof(int2) * (size_t)vb);
+  A((void**)&b->d_order2, 4 * (size_t)count);
   A(&b->adj_ws, adj_ws_bytes(b->dtype, nb, vb));
   A((void**)&b->d_adj_out, sizeof(vx::AdjOut) * count);
   A((void**)&b->aniso_ws, 8 * (3 * (size_t)nb + (size_t)count + 8));
@@ -1041,6 +1092,13 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   cudaMemcpyAsync(b->face0, face.data(), 4 * (size_t)hb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b->vout0, vout.data(), 12 * (size_t)vb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b->ffirst0, ff.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, s);
+  b->n_large = -1;
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    vx_batch_destroy(b);
+    return fail(VX_ERR_CUDA, "vx_batch_create: stream or event creation failed");
+  }
   b->threads = 256;
   b->smem_bytes = 220 * 1024;
   b->tuned = false;
@@ -1062,6 +1120,10 @@ vx_status vx_batch_destroy(vx_batch b) {
                   b->adj_ws, b->d_adj_out, b->wrapk, b->aniso_ws, b->Xtune, b->gXp, b->gXm,
                   b->gdC, b->gaws, b->gout, b->vnb, b->vfc, b->ccnt, b->ccor, b->cedge};
   if (b->gexec2) cudaGraphExecDestroy(b->gexec2);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->d_order2) cudaFree(b->d_order2);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -1207,16 +1269,91 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(b->count, occ * sms);
   b->smem_bytes = smem;
+  // Large tissues (not resident in shared memory at this allocation, and
+  // within the cluster body's per-thread share) go to the cluster kernel,
+  // largest first; the rest to the CTA kernel.  The SMs are shared in
+  // proportion to the cells of each part.
+  std::vector<int> large, rest;
+  double w_large = 0.0, w_all = 0.0;
+  for (int k : b->order) {
+    const BatchDesc& d = b->desc[k];
+    const size_t need = f64 ? vx::batch_res_bytes<vx::PolF64>(d.n, d.V, d.E, d.HE, threads)
+                            : vx::batch_res_bytes<vx::PolF32>(d.n, d.V, d.E, d.HE, threads);
+    w_all += d.n;
+    if (need > (size_t)smem && d.n <= vx::kMcMaxC * vx::kMcT * vx::kMcNR) {
+      large.push_back(k);
+      w_large += d.n;
+    } else {
+      rest.push_back(k);
+    }
+  }
+  const int m = (int)large.size();
+  std::vector<int> order2(large);
+  order2.insert(order2.end(), rest.begin(), rest.end());
+  if (order2 != b->order2) {
+    const cudaError_t ce = cudaMemcpyAsync(b->d_order2, order2.data(), 4 * order2.size(),
+                                           cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return fail(VX_ERR_CUDA, "order upload");
+    b->order2 = order2;
+  }
+  int gc = 0;  // clusters for the large tissues
+  cudaLaunchConfig_t ccfg = {};
+  cudaLaunchAttribute cattr[1];
+  if (m > 0) {
+    auto kern = f64 ? vx::k_min_cluster_batch<vx::PolF64> : vx::k_min_cluster_batch<vx::PolF32>;
+    ccfg.blockDim = dim3(vx::kMcT, 1, 1);
+    ccfg.gridDim = dim3(vx::kMcNR, 1, 1);
+    cattr[0].id = cudaLaunchAttributeClusterDimension;
+    cattr[0].val.clusterDim.x = vx::kMcNR;
+    cattr[0].val.clusterDim.y = 1;
+    cattr[0].val.clusterDim.z = 1;
+    ccfg.attrs = cattr;
+    ccfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &ccfg) != cudaSuccess || nc < 1)
+      return fail(VX_ERR_CUDA, "cluster kernel cannot be resident");
+    const int share = (int)std::lround(sms * (rest.empty() ? 1.0 : w_large / w_all) / vx::kMcNR);
+    gc = std::max(1, std::min({m, nc, share}));
+    ccfg.gridDim = dim3(vx::kMcNR * gc, 1, 1);
+  }
+  const int sm_left = std::max(1, sms - gc * vx::kMcNR);
+  const int grid = rest.empty() ? 0 : std::max(1, std::min((int)rest.size(), occ * sm_left));
   vx::BatchArgs a = make_batch_args(b, X, p, mp);
+  vx::BatchArgs al = a;   // the cluster kernel's queue
+  al.order = b->d_order2;
+  al.count = m;
+  al.counter = b->d_counter + 1;
+  a.order = b->d_order2 + m;
+  a.count = (int)rest.size();
   auto enqueue = [&]() -> cudaError_t {
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4, s);
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 8, s);
     if (e != cudaSuccess) return e;
-    e = f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
-            : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
-    if (e != cudaSuccess || !mp.wrap) return e;
-    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(a, X, b->wrapk, b->d_out);
+    if (m > 0) {
+      e = cudaEventRecord(b->ev_fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+      if (e == cudaSuccess) {
+        ccfg.stream = b->side;
+        e = f64 ? cudaLaunchKernelEx(&ccfg, vx::k_min_cluster_batch<vx::PolF64>, al)
+                : cudaLaunchKernelEx(&ccfg, vx::k_min_cluster_batch<vx::PolF32>, al);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+      if (e != cudaSuccess) return e;
+    }
+    if (grid > 0) {
+      e = f64 ? vx::launch_batch<vx::PolF64>(a, threads, grid, smem, s)
+              : vx::launch_batch<vx::PolF32>(a, threads, grid, smem, s);
+      if (e != cudaSuccess) return e;
+    }
+    if (m > 0) {
+      e = cudaStreamWaitEvent(s, b->ev_join, 0);
+      if (e != cudaSuccess) return e;
+    }
+    if (!mp.wrap) return cudaSuccess;
+    vx::BatchArgs aw = a;   // the wrap covers every tissue
+    aw.count = b->count;
+    vx::k_wrap_batch<<<std::min(b->count, 4 * sms), 256, 0, s>>>(aw, X, b->wrapk, b->d_out);
     return cudaGetLastError();
   };
   cudaError_t e;
@@ -1224,10 +1361,11 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
     e = enqueue();
   } else {
     // Replay the captured launch when the arguments are unchanged.
-    std::vector<unsigned char> key(sizeof(a) + 2 * sizeof(int));
+    std::vector<unsigned char> key(2 * sizeof(a) + 4 * sizeof(int));
+    const int ints[4] = {threads, grid, gc, m};
     std::memcpy(key.data(), &a, sizeof(a));
-    std::memcpy(key.data() + sizeof(a), &threads, sizeof(int));
-    std::memcpy(key.data() + sizeof(a) + sizeof(int), &grid, sizeof(int));
+    std::memcpy(key.data() + sizeof(a), &al, sizeof(al));
+    std::memcpy(key.data() + 2 * sizeof(a), ints, sizeof(ints));
     if (!b->gexec || !same_key(b->gkey, key.data(), key.size())) {
       if (b->gexec) cudaGraphExecDestroy(b->gexec);
       b->gexec = nullptr;
