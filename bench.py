@@ -480,12 +480,12 @@ def bulk_forces_metric(vx, torch, peak, n=1_000_000, steps=10):
     achieved = 112.0 * n / (med * 1e-3) / 1e9
     out = {"metric": "vertex-force evals/s", "unit": "vertex-force evals/s",
            "value": t.V / (med * 1e-3), "ms_per_call": med,
-           "workload": f"one {n}-cell periodic Voronoi tissue ({t.V} vertices), FP32 hi/lo, "
+           "workload": f"one {n}-cell periodic Voronoi tissue ({t.V} vertices), FP32 tissue, "
                        "per-edge Lambda, energy + forces per call (vx_energy_forces), L2 flushed "
                        f"(256 MiB write) before every call, median of {steps} graph-replayed calls",
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "bytes_per_call": "112 n",
-                        "kernels": "k_load_X, k_cells, k_vertices, k_sum_energy"}}
+                        "kernels": "k_ef_cells, k_ef_vertices, k_ef_sum"}}
     t.close()
     return out
 
