@@ -357,33 +357,6 @@ cudaError_t rebuild_flat(vx_tissue_s* t, cudaStream_t s) {
 
 // --------------------------------------------------- bulk evaluation
 
-// Positions read straight from the caller's FP64 array (no conversion
-// pass); each edge vector is formed in FP64 and rounded once to R, the rest
-// of the arithmetic is in R.  For R = float this gives the hi/lo path's
-// differences or better; for R = double it is PolF64.
-template <class R_>
-struct PolIn64 {
-  using R = R_;
-  using Pos = double2;
-  struct Box { double Lx, Ly; };
-  static __host__ __device__ Box make_box(double Lx, double Ly) { return Box{Lx, Ly}; }
-  static __device__ __forceinline__ void diff(const Pos& t, const Pos& s, int ox, int oy,
-                                              const Box& b, R& dx, R& dy) {
-    dx = (R)((t.x + ox * b.Lx) - s.x);
-    dy = (R)((t.y + oy * b.Ly) - s.y);
-  }
-  static __device__ __forceinline__ void add(Pos& p, R dx, R dy) {
-    p.x += dx;
-    p.y += dy;
-  }
-  static __device__ __forceinline__ double2 to_d(const Pos& p) { return p; }
-  static __device__ __forceinline__ Pos from_d(double x, double y) { return make_double2(x, y); }
-  static __device__ __forceinline__ R rsqrt(R x) {
-    if constexpr (std::is_same<R, float>::value) return rsqrtf(x);
-    else return 1.0 / sqrt(x);
-  }
-};
-
 // Per cell: (cA, cP) and the cell part of the energy (block partials in
 // partE[2b], inverted cells in partE[2b + 1]); two cells per thread with
 // both gathers in flight.
@@ -442,7 +415,9 @@ __global__ void __launch_bounds__(256) k_ef_vertices(View<P> v,
                                                      double2* __restrict__ F, double* partL) {
   using R = typename P::R;
   __shared__ double red[32];
-  double el[1] = {0};
+  // per-thread sums of positive terms in R (a handful per thread), the
+  // block and grid stages in FP64
+  R elr = 0;
   auto one = [&](int i, const VGather<P>& g) {
     R fx, fy;
     vertex_compute(v, g, fx, fy);
@@ -452,7 +427,7 @@ __global__ void __launch_bounds__(256) k_ef_vertices(View<P> v,
       for (int a = 0; a < 3; ++a) {
         R dx, dy;
         P::diff(g.Xj[a], g.Xi, tgt_ox(g.tg[a]), tgt_oy(g.tg[a]), v.box, dx, dy);
-        el[0] += 0.5 * (double)g.la[a] * (double)sqrt(dx * dx + dy * dy);
+        elr += (R)0.5 * g.la[a] * sqrt(dx * dx + dy * dy);
       }
     }
   };
@@ -466,6 +441,7 @@ __global__ void __launch_bounds__(256) k_ef_vertices(View<P> v,
     if (i1 < v.V) one(i1, g1);
   }
   if (partL) {
+    double el[1] = {(double)elr};
     block_sum<1>(el, red);
     if (threadIdx.x == 0) partL[blockIdx.x] = el[0];
   }
@@ -482,59 +458,27 @@ __global__ void k_ef_sum(const double* partE, int nbc, const double* partL, int 
   if (threadIdx.x == 0) *E = s[0];
 }
 
+// Energy and forces of one tissue: the positions converted once into the
+// tissue's precision (hi/lo pairs on FP32 tissues: FP64 arithmetic, slow on
+// this GPU, is then needed per vertex only, not per edge), then one
+// gathered pass per cell and one per vertex.
 template <class P>
 static vx_status energy_forces_impl(vx_tissue_s* t, const double* X, const ParamsD& prm,
                                     double* F, double* E, cudaStream_t s) {
   using R = typename P::R;
   const int th = 256;
-  if ((reinterpret_cast<uintptr_t>(X) & 15) == 0) {
-    // positions read in place (16-byte aligned double2), one pass per cell
-    // and one per vertex
-    View<PolIn64<R>> v;
-    {
-      const View<P> w = make_view<P>(t);
-      v.tgt = w.tgt;
-      v.nxt = w.nxt;
-      v.face = w.face;
-      v.vout = w.vout;
-      v.ffirst = w.ffirst;
-      v.vnb = w.vnb;
-      v.vfc = w.vfc;
-      v.ccnt = w.ccnt;
-      v.ccor = w.ccor;
-      v.cedge = w.cedge;
-    }
-    v.X = reinterpret_cast<double2*>(const_cast<double*>(X));
-    v.n = t->n;
-    v.V = t->V;
-    v.E = t->E;
-    v.box = PolIn64<R>::make_box(t->Lx, t->Ly);
-    v.Lx = t->Lx;
-    v.Ly = t->Ly;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int gc = std::min(grid_for(t->n, 2 * th), 8 * sms);
-    const int gv = std::min(grid_for(t->V, 2 * th), 8 * sms);
-    double* partL = t->partE + 2 * (size_t)gc;   // fits: 2 gc + gv <= 3 ((n + 255) / 256 + 1)
-    k_ef_cells<PolIn64<R>><<<gc, th, 0, s>>>(v, prm, (R2T<R>*)t->cellc, E ? t->partE : nullptr);
-    k_ef_vertices<PolIn64<R>, double><<<gv, th, 0, s>>>(v, (const R2T<R>*)t->cellc, prm.lam,
-                                                        prm.lam_s, (double2*)F,
-                                                        E ? partL : nullptr);
-    if (E) k_ef_sum<<<1, 256, 0, s>>>(t->partE, gc, partL, gv, E);
-    return cudaGetLastError() == cudaSuccess ? VX_OK : VX_ERR_CUDA;
-  }
   View<P> v = make_view<P>(t);
-  k_load_X<P><<<grid_for(t->V, th), th, 0, s>>>(X, v.X, t->V);
-  const int nbc = grid_for(t->n, th);
-  k_cells<P><<<nbc, th, 0, s>>>(v, prm, (R2T<R>*)t->cellc, t->shortbits, 0.0, nullptr,
-                                E ? t->partE : nullptr);
-  if (F) {
-    MinParams mp = {};
-    k_vertices<P, double2><<<grid_for(t->V, th), th, 0, s>>>(
-        v, (const R2T<R>*)t->cellc, prm.lam, prm.lam_s, (double2*)F, nullptr, nullptr, nullptr, mp);
-  }
-  if (E) k_sum_energy<<<1, 32, 0, s>>>(t->partE, nbc, E, nullptr);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int gc = std::min(grid_for(t->n, 2 * th), 8 * sms);
+  const int gv = std::min(grid_for(t->V, 2 * th), 8 * sms);
+  double* partL = t->partE + 2 * (size_t)gc;   // fits: 2 gc + gv <= 3 ((n + 255) / 256 + 1)
+  k_load_X<P><<<std::min(grid_for(t->V, th), 8 * sms), th, 0, s>>>(X, v.X, t->V);
+  k_ef_cells<P><<<gc, th, 0, s>>>(v, prm, (R2T<R>*)t->cellc, E ? t->partE : nullptr);
+  k_ef_vertices<P, double><<<gv, th, 0, s>>>(v, (const R2T<R>*)t->cellc, prm.lam, prm.lam_s,
+                                             (double2*)F, E ? partL : nullptr);
+  if (E) k_ef_sum<<<1, 256, 0, s>>>(t->partE, gc, partL, gv, E);
   return cudaGetLastError() == cudaSuccess ? VX_OK : VX_ERR_CUDA;
 }
 

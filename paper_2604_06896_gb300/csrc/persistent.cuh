@@ -977,7 +977,11 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
       aniso_dC_dQ(Q, mp.cost_data, G);
       aniso_nudge_pass(vw, tid, T, mp.aniso_ws, G[0], G[1], G[2], (double2*)mp.aniso_nudge);
     }
+    // F.F, F.v, v.v, max |F|^2: FP32 tissues sum their per-thread parts in
+    // FP32 and combine warps in FP64 (FP64 issues slowly on this GPU)
+    constexpr bool kF32 = std::is_same<R, float>::value;
     double red[4] = {0, 0, 0, 0};
+    float redf[4] = {0, 0, 0, 0};
     auto vertex_tail = [&](int i, R fx, R fy) {
       if (nudged_v2v) {
         double gx, gy;
@@ -995,11 +999,19 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
       f.y = fy;
       frc[i] = f;
       const R2 u = vel[i];
-      const double f2 = (double)(fx * fx + fy * fy);
-      red[0] += f2;
-      red[1] += (double)(fx * u.x + fy * u.y);
-      red[2] += (double)(u.x * u.x + u.y * u.y);
-      red[3] = fmax(red[3], f2);
+      if constexpr (kF32) {
+        const float f2 = fx * fx + fy * fy;
+        redf[0] += f2;
+        redf[1] += fx * u.x + fy * u.y;
+        redf[2] += u.x * u.x + u.y * u.y;
+        redf[3] = fmaxf(redf[3], f2);
+      } else {
+        const double f2 = (double)(fx * fx + fy * fy);
+        red[0] += f2;
+        red[1] += (double)(fx * u.x + fy * u.y);
+        red[2] += (double)(u.x * u.x + u.y * u.y);
+        red[3] = fmax(red[3], f2);
+      }
     };
     // two vertices per thread with both gathers in flight
     for (int i0 = tid; i0 < V; i0 += 2 * T) {
@@ -1015,8 +1027,11 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
         vertex_tail(i1, fx, fy);
       }
     }
-    tm.template reduce<4>(red, sl.a, 1);
-    fmx = sqrt(red[3]);
+    if constexpr (kF32)
+      tm.template reduce_f<4>(redf, red, sl.a, 1);
+    else
+      tm.template reduce<4>(red, sl.a, 1);
+    fmx = kF32 ? (double)sqrtf((float)red[3]) : sqrt(red[3]);
     if (!(fmx == fmx) || isinf(fmx)) {
       status = VX_ERR_NONFINITE;
       break;
