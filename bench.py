@@ -41,7 +41,10 @@ MODULI = ("dimensionless moduli: K_A = 1/A0, K_P = 1, P0 = p0*sqrt(A0), Lambda =
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an
 # ncu capture of the current kernel (None until the changed kernel is
 # captured again)
-TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the c2 kernel
+# (ncu capture of 300 iterations; the traffic is the one-off load of the
+# tissues' state into L2 and does not grow with the iteration count)
+TRAFFIC_BYTES = 10_570_496
 MAX_ITER = 20_000   # per relaxation: a fixed budget (the tolerance is not reached)
 
 
@@ -684,9 +687,9 @@ def run_gpu(args):
                      "note": "algorithmic bytes per iteration x iterations / launch time, against "
                              "the measured HBM copy rate (of measured); the tissue state (~2 MB "
                              "per relaxation) stays in L2 and the kernel is bound by L2 latency "
-                             "and barriers, not by bandwidth; traffic (dram bytes read + written "
-                             "per launch, one ncu capture) is null until the changed kernel is "
-                             "captured again"},
+                             "and barriers, not by bandwidth; traffic = dram bytes read + written "
+                             "per launch from one ncu capture (300 iterations: the one-off state "
+                             "load, which does not grow with the iteration count)"},
         "equilibrium_gradient": grad,
         "bulk_forces": bulk,
         "batched_forward": batched,
