@@ -125,6 +125,15 @@ __device__ __forceinline__ void batch_rebuild_flat(const View<P>& v) {
 
 __host__ __device__ inline size_t b16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// A tissue's slice of a per-cell or per-vertex work array that holds 16
+// bytes per element: the slice starts at 16 bytes x the tissue's base in
+// either precision, so FP32 phases of one tissue and FP64 phases of another
+// never overlap.
+template <class T>
+__host__ __device__ inline T* slice16(void* buf, size_t base) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(buf) + 16 * base);
+}
+
 // Shared memory a resident tissue needs in the batched kernel.
 template <class P>
 __host__ __device__ size_t batch_res_bytes(int n, int V, int E, int HE, int T) {
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
       v.ffirst = gff;
       batch_flat(g, d, v);
       Slots sl = {gslots[0], gslots[1], gslots[2]};
-      min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+      min_body_mem<P, T>(v, slice16<R2>(g.cellc, d.cbase), slice16<R2>(g.vel, d.vbase), slice16<R2>(g.frc, d.vbase),
                          prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xin,
                          Xo, g.out + g.order[k]);
     }
@@ -390,7 +399,7 @@ __device__ __noinline__ void grad_free(const BatchGradArgs& a, const BatchDesc& 
   using R2 = typename Vec2Of<typename P::R>::T;
   const BatchArgs& g = a.b;
   View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
-  min_body_mem<P, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+  min_body_mem<P, T>(v, slice16<R2>(g.cellc, d.cbase), slice16<R2>(g.vel, d.vbase), slice16<R2>(g.frc, d.vbase),
                      prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xk, Xk,
                      out);
   __syncthreads();
@@ -470,7 +479,7 @@ __device__ __noinline__ void batch_nudged(const BatchGradArgs& a, const BatchDes
   const BatchArgs& g = a.b;
   View<Q> v = batch_view<Q>(g, d, (typename Q::Pos*)g.Xw + d.vbase);
   mp.nudge_s = s;
-  min_body_mem<Q, T>(v, (R2*)g.cellc + d.cbase, (R2*)g.vel + d.vbase, (R2*)g.frc + d.vbase,
+  min_body_mem<Q, T>(v, slice16<R2>(g.cellc, d.cbase), slice16<R2>(g.vel, d.vbase), slice16<R2>(g.frc, d.vbase),
                      prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, mp, Xs, Xout,
                      out);
   __syncthreads();
@@ -574,7 +583,7 @@ __device__ __noinline__ void gc_relax(const Team& tm, const BatchGradArgs& a, co
   for (int w = tm.first(); w < (d.V + 31) / 32; w += tm.stride()) tb[w] = 0;
   View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
   tm.sync();
-  min_body<P, Team, kGcMaxC>(tm, v, (R2*)g.cellc + d.cbase, prm.lam, sb, tb, sl, prm, mp, Xin,
+  min_body<P, Team, kGcMaxC>(tm, v, slice16<R2>(g.cellc, d.cbase), prm.lam, sb, tb, sl, prm, mp, Xin,
                              Xout, out);
   tm.sync();
 }
@@ -885,7 +894,7 @@ __global__ void __launch_bounds__(kMcT) k_min_cluster_batch(BatchArgs g) {
     sl.dirty_cap = kMcDirty;
     View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
     tm.sync();
-    min_body<P, Team, kMcMaxC>(tm, v, (R2*)g.cellc + d.cbase, prm.lam, sb, tb, sl, prm, g.mp,
+    min_body<P, Team, kMcMaxC>(tm, v, slice16<R2>(g.cellc, d.cbase), prm.lam, sb, tb, sl, prm, g.mp,
                                g.X + 2 * (size_t)d.vbase, g.Xout + 2 * (size_t)d.vbase,
                                g.out + tk);
     tm.sync();

@@ -170,23 +170,35 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
                                               const ParamsD* prm = nullptr) {
   using R = typename P::R;
   if (v.ccor) {
-    // Corners in chunks of four: the corner words arrive in one 16-byte load
-    // and the four position loads are issued before any is used, so a cell
-    // costs two load latencies per chunk instead of two per corner.
+    // The count and the first eight corner words (two 16-byte loads) are
+    // loaded together; each chunk of four corners issues its four position
+    // loads and the next chunk's first before any is used: three load
+    // latencies for a cell of up to eight corners.
     using Pos = typename P::Pos;
-    const int m = v.ccnt[c];
     const uint32_t* cor = v.ccor + (size_t)c * kMaxCorners;
     const int32_t* ced = v.cedge + (size_t)c * kMaxCorners;
+    const uint4 wa = reinterpret_cast<const uint4*>(cor)[0];
+    const uint4 wb = reinterpret_cast<const uint4*>(cor)[1];
+    const int m = v.ccnt[c];
     R qx = 0, qy = 0, A2 = 0, pp = 0;
     bool flagged = false;
     double el = 0.0;
     Pos X0;
     for (int base = 0; base < m; base += 4) {
-      const uint4 w0 = reinterpret_cast<const uint4*>(cor + base)[0];
-      const uint32_t cw[4] = {w0.x, w0.y, w0.z, w0.w};
-      Pos Xc[4];
+      uint32_t cw[5];
+      if (base == 0) {
+        cw[0] = wa.x; cw[1] = wa.y; cw[2] = wa.z; cw[3] = wa.w; cw[4] = wb.x;
+      } else if (base == 4) {
+        cw[0] = wb.x; cw[1] = wb.y; cw[2] = wb.z; cw[3] = wb.w;
+        cw[4] = m > 8 ? cor[8] : 0u;
+      } else {
+        const uint4 w = reinterpret_cast<const uint4*>(cor + base)[0];
+        cw[0] = w.x; cw[1] = w.y; cw[2] = w.z; cw[3] = w.w;
+        cw[4] = base + 4 < m ? cor[base + 4] : 0u;
+      }
+      Pos Xc[5];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < 5; ++k)
         if (base + k < m) Xc[k] = v.X[tgt_v(cw[k])];
       if (base == 0) X0 = Xc[0];
 #pragma unroll
@@ -194,13 +206,8 @@ __device__ __forceinline__ bool cell_geometry(const View<P>& v, int c, typename 
         const int kk = base + k;  // edge from corner kk to corner kk + 1
         if (kk < m) {
           R nx = 0, ny = 0;
-          if (k < 3) {
-            if (kk + 1 < m)
-              P::diff(Xc[k + 1], X0, tgt_ox(cw[k + 1]), tgt_oy(cw[k + 1]), v.box, nx, ny);
-          } else if (kk + 1 < m) {
-            const uint32_t t = cor[kk + 1];
-            P::diff(v.X[tgt_v(t)], X0, tgt_ox(t), tgt_oy(t), v.box, nx, ny);
-          }
+          if (kk + 1 < m)
+            P::diff(Xc[k + 1], X0, tgt_ox(cw[k + 1]), tgt_oy(cw[k + 1]), v.box, nx, ny);
           // q_kk -> q_{kk+1}; q_0 = 0
           A2 += qx * ny - nx * qy;
           const R ex = nx - qx, ey = ny - qy;

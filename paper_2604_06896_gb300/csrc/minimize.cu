@@ -366,12 +366,20 @@ __global__ void __launch_bounds__(256) k_ef_cells(View<P> v, ParamsD prm,
                                                   double* partE) {
   using R = typename P::R;
   __shared__ double red[32 * 2];
-  double acc[2] = {0, 0};
+  // Arithmetic in R: A and P are R values, so their differences from the
+  // targets lose nothing in R; uniform parameters are converted once (on
+  // FP32 tissues every FP64 operation, conversions included, runs on this
+  // GPU's narrow FP64 pipe).  Per-thread energy sums of a few positive
+  // terms in R, the block and grid stages in FP64.
+  const R ka_s = (R)prm.KA_s, kp_s = (R)prm.KP_s, a0_s = (R)prm.A0_s, p0_s = (R)prm.P0_s;
+  R er = 0;
+  int inv = 0;
   auto finish = [&](int c, R A, R Pp) {
-    const double dA = (double)A - prm.a0(c), dP = (double)Pp - prm.p0(c);
-    cellc[c] = mk2<R>((R)(2.0 * prm.ka(c) * dA), (R)(2.0 * prm.kp(c) * dP));
-    acc[0] += prm.ka(c) * dA * dA + prm.kp(c) * dP * dP;
-    acc[1] += (A <= 0) ? 1.0 : 0.0;
+    const R ka = prm.KA ? (R)prm.KA[c] : ka_s, kp = prm.KP ? (R)prm.KP[c] : kp_s;
+    const R dA = A - (prm.A0 ? (R)prm.A0[c] : a0_s), dP = Pp - (prm.P0 ? (R)prm.P0[c] : p0_s);
+    cellc[c] = mk2<R>((R)2 * ka * dA, (R)2 * kp * dP);
+    er += ka * dA * dA + kp * dP * dP;
+    inv += (A <= 0) ? 1 : 0;
   };
   const int st = gridDim.x * blockDim.x;
   for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < v.n; c0 += 2 * st) {
@@ -397,6 +405,7 @@ __global__ void __launch_bounds__(256) k_ef_cells(View<P> v, ParamsD prm,
     }
   }
   if (partE) {
+    double acc[2] = {(double)er, (double)inv};
     block_sum<2>(acc, red);
     if (threadIdx.x == 0) {
       partE[2 * blockIdx.x] = acc[0];
