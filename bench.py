@@ -297,7 +297,7 @@ def c4_oracle_errors(check):
                     "pipeline is measured by tests/test_gpu_c4.py"}
 
 
-def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000):
+def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, compare=True):
     """The batched forward workload: 512 periodic Voronoi tissues of
     log-uniform size in [200, 5000] cells (7.5e5 cells in all), per-tissue
     p0 ~ U(3.5, 4.0), per-edge Lambda ~ U(0, 0.1), FP32, FIRE + T1 to
@@ -338,6 +338,11 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000):
 
     allidx = list(range(len(batch)))
     value, ms_step, rs = run_batched(allidx, steps)
+    if not compare:
+        return {"metric": "vertex-force evals/s", "value": value, "ms_per_step": ms_step,
+                "converged": int(sum(r.status == 0 for r in rs)),
+                "force_evals_per_tissue": [int(min(r.force_evals for r in rs)),
+                                           int(max(r.force_evals for r in rs))]}
     sub = allidx[::subset_every]
     sub_value, sub_ms, _ = run_batched(sub, 1)
     plain_ms, plain_evals = 0.0, 0
@@ -789,6 +794,9 @@ def main():
     ap.add_argument("--bulk-only", action="store_true",
                     help="only the bulk energy + force line (for ncu)")
     ap.add_argument("--bulk-cells", type=int, default=1_000_000)
+    ap.add_argument("--c3-only", action="store_true",
+                    help="only the batched forward workload, without the plain-path comparison "
+                         "(for a launch list)")
     ap.add_argument("--bulk-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true", help="small fixed runs for ncu")
     ap.add_argument("--profile-iters", type=int, default=2000)
@@ -799,6 +807,10 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.c3_only:
+        import torch
+        import paper_2604_06896_gb300 as vx
+        print(json.dumps(batched_forward_metric(vx, torch, steps=1, compare=False)))
     elif args.bulk_only:
         import torch
         import paper_2604_06896_gb300 as vx

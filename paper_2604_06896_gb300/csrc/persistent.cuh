@@ -902,10 +902,15 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
   const R lminR = (R)mp.l_min;
   double dt = mp.dt0, alpha = mp.alpha0, fmx = 0;
   int npos = 0, below = 0, it = 0, status = VX_NOT_CONVERGED, n_t1 = 0, n_st = 0;
+  // uniform parameters converted once (FP64 operations, conversions
+  // included, are slow on this GPU); the values are those of the per-cell
+  // expressions
+  const R ka2_s = (R)(2.0 * prm.KA_s), kp2_s = (R)(2.0 * prm.KP_s);
+  const R a0_s = (R)prm.A0_s, p0_s = (R)prm.P0_s;
   auto cell_coef = [&](int c, R A, R Pp) {
     R2 cc;
-    cc.x = (R)(2.0 * prm.ka(c)) * (A - (R)prm.a0(c));
-    cc.y = (R)(2.0 * prm.kp(c)) * (Pp - (R)prm.p0(c));
+    cc.x = (prm.KA ? (R)(2.0 * prm.KA[c]) : ka2_s) * (A - (prm.A0 ? (R)prm.A0[c] : a0_s));
+    cc.y = (prm.KP ? (R)(2.0 * prm.KP[c]) : kp2_s) * (Pp - (prm.P0 ? (R)prm.P0[c] : p0_s));
     cell[c] = cc;
   };
   auto cell_pass = [&](R lm) -> bool {
