@@ -75,15 +75,23 @@ struct PolF32 {
     b.Lyl = (float)(Ly - (double)b.Lyh);
     return b;
   }
+  // A small integer as a float without a conversion instruction (those run
+  // on the narrow FP64 pipe of this GPU): 1.5 * 2^23 + o is exact in a float
+  // for |o| < 2^22 and its bit pattern is 0x4B400000 + o; subtracting
+  // 1.5 * 2^23 leaves o exactly.
+  static __device__ __forceinline__ float small_int(int o) {
+    return __fsub_rn(__int_as_float(0x4B400000 + o), 12582912.0f);
+  }
   // a_hi + a_lo - b_hi - b_lo + o (Lh + Ll), rounded once at the end.
   static __device__ __forceinline__ float dd(float ah, float al, float bh, float bl, int o,
                                              float Lh, float Ll) {
     const float s = __fsub_rn(ah, bh);
     const float e = two_sum_err(ah, -bh, s);
-    const float oL = (float)o * Lh;            // exact: o in {-2..2}
+    const float of = small_int(o);
+    const float oL = of * Lh;                  // exact: o in {-2..2}
     const float t = __fadd_rn(s, oL);
     const float e2 = two_sum_err(s, oL, t);
-    return __fadd_rn(t, __fadd_rn(__fadd_rn(e, e2), __fadd_rn(__fsub_rn(al, bl), (float)o * Ll)));
+    return __fadd_rn(t, __fadd_rn(__fadd_rn(e, e2), __fadd_rn(__fsub_rn(al, bl), of * Ll)));
   }
   static __device__ __forceinline__ void diff(const Pos& t, const Pos& s, int ox, int oy,
                                               const Box& b, R& dx, R& dy) {
