@@ -510,9 +510,10 @@ vx_status vx_equilibrium_grad_batched(vx_batch b, const double* Xstar, const vx_
  * (go->mode VX_EP_CENTERED) or E + beta C (VX_EP_FORWARD) from X* under
  * go->inner without T1, in FP64 arithmetic when go->ep_f64, then the
  * difference of d_theta E over beta.  Each tissue is run by one CTA, or
- * by one 16-CTA cluster when every tissue has at least 4,096 cells and at
- * most 12,288 (free_opts->path VX_PATH_RESIDENT / VX_PATH_CLUSTER forces
- * one or the other; CLUSTER with a larger tissue is VX_ERR_INVALID_ARG).
+ * by one cluster (8 CTAs up to 10,240 cells, 16 up to 12,288) when every
+ * tissue has at least 4,096 cells and at most 12,288 (free_opts->path
+ * VX_PATH_RESIDENT forces one CTA, VX_PATH_CLUSTER 16-CTA clusters;
+ * CLUSTER with a tissue above 12,288 cells is VX_ERR_INVALID_ARG).
  * X dev float64 [sum V][2] in/out
  * (X*, wrapped per free_opts->wrap).  Gradients (each may be NULL): ga_*
  * adjoint, ge_* EP; lambda dev [sum E], A0 and P0 dev [sum n].  r host

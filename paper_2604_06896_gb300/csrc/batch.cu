@@ -567,11 +567,14 @@ __global__ void __launch_bounds__(T) k_grad_batch(BatchGradArgs a) {
 // single-tissue cluster path on them (each thread owns up to MAXC cells and
 // 2 MAXC vertices; the tissue lives in L2 with its flat tables).  The phases
 // are the ones of k_grad_batch, out of line.
-constexpr int kGcT = 256, kGcNR = 16, kGcMaxC = 3, kGcDirty = 1024;
+constexpr int kGcT = 256, kGcDirty = 1024;
+// cluster sizes and per-thread cell shares: 8 CTAs (portable; more clusters
+// resident at once) for tissues up to 5 x 256 x 8 cells, else 16
+constexpr int kGcNR8 = 8, kGcMaxC8 = 5, kGcNR16 = 16, kGcMaxC16 = 3;
 // Smallest tissue for which the automatic choice takes a cluster per tissue.
 constexpr int kClusterMinCells = 4096;
 
-template <class P, class Team>
+template <class P, int MAXC, class Team>
 __device__ __noinline__ void gc_relax(const Team& tm, const BatchGradArgs& a, const BatchDesc& d,
                                       const ParamsD& prm, const MinParams& mp, Slots sl,
                                       const double* Xin, double* Xout, MinOut* out) {
@@ -583,7 +586,7 @@ __device__ __noinline__ void gc_relax(const Team& tm, const BatchGradArgs& a, co
   for (int w = tm.first(); w < (d.V + 31) / 32; w += tm.stride()) tb[w] = 0;
   View<P> v = batch_view<P>(g, d, (typename P::Pos*)g.Xw + d.vbase);
   tm.sync();
-  min_body<P, Team, kGcMaxC>(tm, v, slice16<R2>(g.cellc, d.cbase), prm.lam, sb, tb, sl, prm, mp, Xin,
+  min_body<P, Team, MAXC>(tm, v, slice16<R2>(g.cellc, d.cbase), prm.lam, sb, tb, sl, prm, mp, Xin,
                              Xout, out);
   tm.sync();
 }
@@ -633,7 +636,7 @@ __device__ __noinline__ double gc_cost(const Team& tm, const BatchGradArgs& a, c
   return cost;
 }
 
-template <class P, class Team>
+template <class P, int MAXC, class Team>
 __device__ __noinline__ void gc_adjoint(const Team& tm, const BatchGradArgs& a,
                                         const BatchDesc& d, const ParamsD& prm, Slots sl,
                                         const double* Xk, const double2* dC, AdjOut* out) {
@@ -649,7 +652,7 @@ __device__ __noinline__ void gc_adjoint(const Team& tm, const BatchGradArgs& a,
   ap.g_lam = a.ga_lam ? a.ga_lam + d.ebase : nullptr;
   ap.g_A0 = a.ga_A0 ? a.ga_A0 + d.cbase : nullptr;
   ap.g_P0 = a.ga_P0 ? a.ga_P0 + d.cbase : nullptr;
-  adj_body<P, Team, kGcMaxC>(tm, v, (R4*)a.cell4 + d.cbase, prm.lam, (R2*)a.ap + d.vbase, sl, prm,
+  adj_body<P, Team, MAXC>(tm, v, (R4*)a.cell4 + d.cbase, prm.lam, (R2*)a.ap + d.vbase, sl, prm,
                              ap, Xk, out);
   tm.sync();
 }
@@ -675,9 +678,9 @@ __device__ __noinline__ void gc_ep_diff(const Team& tm, const BatchGradArgs& a,
   tm.sync();
 }
 
-template <class P>
+template <class P, int NR, int MAXC>
 __global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
-  using Team = ClusterTeam<kGcT, kGcNR>;
+  using Team = ClusterTeam<kGcT, NR>;
   __shared__ int item;
   __shared__ double slots[3][4 * (kGcT / 32 + 2)];
   __shared__ int dirty[kGcDirty];
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
     sl.dirty = dirty;
     sl.dirty_cap = kGcDirty;
     double* Xk = (double*)g.X + 2 * (size_t)d.vbase;
-    gc_relax<P>(tm, a, d, prm, g.mp, sl, Xk, Xk, &o->free);
+    gc_relax<P, MAXC>(tm, a, d, prm, g.mp, sl, Xk, Xk, &o->free);
     double2* dC = (double2*)a.dC + d.vbase;
     double2* acent = (double2*)(a.aws + 4 * (size_t)d.cbase);
     int* akk = (int*)(a.aws + 4 * (size_t)d.cbase + 2 * (size_t)d.n);
@@ -710,7 +713,7 @@ __global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
     mpn.aniso_nudge = mpn.cost == 2 ? (double*)dC : nullptr;
     const double cost = gc_cost(tm, a, d, mpn, sl, Xk, dC, acent, akk);
     if (tm.leader()) o->cost = cost;
-    if (a.do_adjoint) gc_adjoint<P>(tm, a, d, prm, sl, Xk, dC, &o->adj);
+    if (a.do_adjoint) gc_adjoint<P, MAXC>(tm, a, d, prm, sl, Xk, dC, &o->adj);
     if (a.do_ep) {
       double* Xp = a.Xp + 2 * (size_t)d.vbase;
       double* Xm = a.Xm + 2 * (size_t)d.vbase;
@@ -718,13 +721,13 @@ __global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
       MinParams mq = mpn;
       mq.nudge_s = sp;
       if (a.ep_f64) {
-        gc_relax<PolF64>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
+        gc_relax<PolF64, MAXC>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
         mq.nudge_s = -sp;
-        if (a.centered) gc_relax<PolF64>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
+        if (a.centered) gc_relax<PolF64, MAXC>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
       } else {
-        gc_relax<P>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
+        gc_relax<P, MAXC>(tm, a, d, prm, mq, sl, Xk, Xp, &o->plus);
         mq.nudge_s = -sp;
-        if (a.centered) gc_relax<P>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
+        if (a.centered) gc_relax<P, MAXC>(tm, a, d, prm, mq, sl, Xk, Xm, &o->minus);
       }
       gc_ep_diff(tm, a, d, prm, Xp, a.centered ? Xm : Xk);
     }
@@ -1652,14 +1655,15 @@ int grad_grid(K kernel, int count) {
 // set and the resident cluster count queried outside any capture; the grid
 // is that many clusters (at most one per tissue).
 template <class K>
-cudaError_t cluster_grid(K kernel, int count, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+cudaError_t cluster_grid(K kernel, int nr, int count, cudaLaunchConfig_t* cfg,
+                         cudaLaunchAttribute* attr) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   *cfg = cudaLaunchConfig_t{};
-  cfg->gridDim = dim3(vx::kGcNR, 1, 1);
+  cfg->gridDim = dim3(nr, 1, 1);
   cfg->blockDim = dim3(vx::kGcT, 1, 1);
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = vx::kGcNR;
+  attr[0].val.clusterDim.x = nr;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg->attrs = attr;
@@ -1668,7 +1672,7 @@ cudaError_t cluster_grid(K kernel, int count, cudaLaunchConfig_t* cfg, cudaLaunc
   e = cudaOccupancyMaxActiveClusters(&nc, kernel, cfg);
   if (e != cudaSuccess) return e;
   if (nc < 1) return cudaErrorInvalidConfiguration;
-  cfg->gridDim = dim3(vx::kGcNR * std::min(count, nc), 1, 1);
+  cfg->gridDim = dim3(nr * std::min(count, nc), 1, 1);
   return cudaSuccess;
 }
 
@@ -1733,15 +1737,19 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
   a.ge_P0 = ge_P0;
   a.out = (vx::BatchGradOut*)b->gout;
   const bool f64 = b->dtype == VX_F64;
-  // Team per tissue: one 16-CTA cluster when every tissue is large (a CTA
-  // alone would run it from L2 on one SM) and fits the cluster body's
-  // per-thread share, else one CTA (fo->path CLUSTER / RESIDENT forces it).
+  // Team per tissue: one cluster when every tissue is large (a CTA alone
+  // would run it from L2 on one SM) and fits the cluster body's per-thread
+  // share (8 CTAs up to 10,240 cells, 16 up to 12,288), else one CTA
+  // (fo->path CLUSTER / RESIDENT forces it).
   int nmin = b->desc[0].n, nmax = b->desc[0].n;
   for (const BatchDesc& d : b->desc) {
     nmin = std::min(nmin, d.n);
     nmax = std::max(nmax, d.n);
   }
-  const bool fits = nmax <= vx::kGcMaxC * vx::kGcT * vx::kGcNR;
+  // VX_PATH_CLUSTER asks for the 16-CTA clusters; the automatic choice
+  // takes 8-CTA clusters where the tissues fit them
+  const bool fits8 = fo->path != VX_PATH_CLUSTER && nmax <= vx::kGcMaxC8 * vx::kGcT * vx::kGcNR8;
+  const bool fits = fits8 || nmax <= vx::kGcMaxC16 * vx::kGcT * vx::kGcNR16;
   if (fo->path == VX_PATH_CLUSTER && !fits)
     return fail(VX_ERR_INVALID_ARG, "a tissue is too large for the cluster-per-tissue kernel");
   const bool use_cluster = fo->path == VX_PATH_CLUSTER ||
@@ -1750,8 +1758,15 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
   cudaLaunchAttribute cattr[1];
   int grid = 0;
   if (use_cluster) {
-    const cudaError_t ce = f64 ? cluster_grid(vx::k_grad_cluster<vx::PolF64>, b->count, &ccfg, cattr)
-                               : cluster_grid(vx::k_grad_cluster<vx::PolF32>, b->count, &ccfg, cattr);
+    using namespace vx;
+    const int nr = fits8 ? kGcNR8 : kGcNR16;
+    cudaError_t ce;
+    if (fits8)
+      ce = f64 ? cluster_grid(k_grad_cluster<PolF64, kGcNR8, kGcMaxC8>, nr, b->count, &ccfg, cattr)
+               : cluster_grid(k_grad_cluster<PolF32, kGcNR8, kGcMaxC8>, nr, b->count, &ccfg, cattr);
+    else
+      ce = f64 ? cluster_grid(k_grad_cluster<PolF64, kGcNR16, kGcMaxC16>, nr, b->count, &ccfg, cattr)
+               : cluster_grid(k_grad_cluster<PolF32, kGcNR16, kGcMaxC16>, nr, b->count, &ccfg, cattr);
     if (ce != cudaSuccess)
       return fail(VX_ERR_CUDA, std::string("cluster kernel: ") + cudaGetErrorString(ce));
     grid = (int)ccfg.gridDim.x;
@@ -1770,8 +1785,13 @@ extern "C" vx_status vx_batch_grad(vx_batch b, double* X, const vx_batch_params*
     if (e != cudaSuccess) return e;
     if (use_cluster) {
       ccfg.stream = st;
-      e = f64 ? cudaLaunchKernelEx(&ccfg, vx::k_grad_cluster<vx::PolF64>, a)
-              : cudaLaunchKernelEx(&ccfg, vx::k_grad_cluster<vx::PolF32>, a);
+      using namespace vx;
+      if (fits8)
+        e = f64 ? cudaLaunchKernelEx(&ccfg, k_grad_cluster<PolF64, kGcNR8, kGcMaxC8>, a)
+                : cudaLaunchKernelEx(&ccfg, k_grad_cluster<PolF32, kGcNR8, kGcMaxC8>, a);
+      else
+        e = f64 ? cudaLaunchKernelEx(&ccfg, k_grad_cluster<PolF64, kGcNR16, kGcMaxC16>, a)
+                : cudaLaunchKernelEx(&ccfg, k_grad_cluster<PolF32, kGcNR16, kGcMaxC16>, a);
     } else {
       if (f64)
         vx::k_grad_batch<vx::PolF64, 256><<<grid, 256, 0, st>>>(a);

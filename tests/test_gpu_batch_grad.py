@@ -148,14 +148,14 @@ def test_batch_grad_vs_oracle(vx):
     b.close()
 
 
-@pytest.mark.parametrize("team,what", [("auto", 3), ("resident", 1)])
+@pytest.mark.parametrize("team,what", [("auto", 3), ("cluster", 1), ("resident", 1)])
 def test_batch_grad_c5_full_size(vx, team, what):
     """The batched inverse-design workload at full size: 64 tissues of
     10,000 cells, FP32, anisotropy cost, per-cell A0 and per-edge tensions,
     free relaxation (T1 on, fixed budget), the adjoint and (what = 3)
-    centred EP with FP64 nudged phases, in one launch: a 16-CTA cluster per
-    tissue (the automatic choice for tissues this large) or one CTA per
-    tissue (forced).  Checked on sampled tissues: the oracle's energy, max
+    centred EP with FP64 nudged phases, in one launch: an 8-CTA cluster per
+    tissue (the automatic choice for tissues this large), a 16-CTA cluster
+    or one CTA per tissue (forced).  Checked on sampled tissues: the oracle's energy, max
     |F| and cost at the returned state agree with the GPU's, and the
     batched adjoint equals the single-tissue adjoint at the same state.
     EP's accuracy is not asserted here: the free relaxations stop at the
