@@ -215,11 +215,14 @@ typedef struct {
                           made are added (a diagnostic of repeated events) */
   double  refine_tol;  /* FP32 tissues, vx_minimize only: when > tol, the
                           solve runs in FP32 arithmetic until max|F| <
-                          refine_tol, then continues from there in FP64
-                          arithmetic to tol (FP32 forces carry ~3e-7
-                          relative rounding, below which FP32 FIRE stalls);
-                          the iteration budget is shared; 0 (default): one
-                          precision throughout                             */
+                          refine_tol, then takes up to 8 Newton steps
+                          X += H^-1 F (F in FP64 arithmetic, H^-1 F by CG on
+                          the Hessian-vector product; a step that does not
+                          lower max|F| is undone) and finishes with FP64
+                          FIRE to tol (FP32 forces carry ~3e-7 relative
+                          rounding, below which FP32 FIRE stalls); the FIRE
+                          budget is shared; 0 (default): one precision
+                          throughout                                       */
 } vx_min_opts;
 
 typedef struct {

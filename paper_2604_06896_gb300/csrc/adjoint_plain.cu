@@ -753,6 +753,81 @@ static vx_status sensitivity_t(vx_tissue_s* t, const double* Xstar, const Params
   return VX_OK;
 }
 
+namespace {
+
+__global__ void k_nt_step(int V, double* X, const double2* d, double* backup) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    const double2 x = make_double2(X[2 * i], X[2 * i + 1]);
+    backup[2 * i] = x.x;
+    backup[2 * i + 1] = x.y;
+    X[2 * i] = x.x + d[i].x;
+    X[2 * i + 1] = x.y + d[i].y;
+  }
+}
+
+__global__ void k_nt_fmax(int V, const double2* F, double* out) {
+  __shared__ double red[kT / 32];
+  double m = 0;
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    const double2 f = F[i];
+    m = fmax(m, f.x * f.x + f.y * f.y);
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+    *out = sqrt(r);
+  }
+}
+
+}  // namespace
+
+vx_status newton_refine(vx_tissue_s* t, double* X, const ParamsD& prm, double tol, int max_steps,
+                        int* steps, double* fmax, cudaStream_t s) {
+  const int V = t->V, nb = (V + kT - 1) / kT;
+  double* F = work_ep(t);                 // [V][2]; the EP region is free here
+  double* backup = F + 2 * (size_t)V;     // [V][2]
+  double* dev_f = backup + 2 * (size_t)V; // one double
+  const int saved = t->dtype;
+  auto residual = [&](double* fm) -> vx_status {
+    t->dtype = VX_F64;
+    vx_status st = energy_forces(t, X, prm, F, nullptr, s);
+    t->dtype = saved;
+    if (st != VX_OK) return st;
+    k_nt_fmax<<<1, kT, 0, s>>>(V, (const double2*)F, dev_f);
+    cudaError_t e = cudaMemcpyAsync(fm, dev_f, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? VX_OK : VX_ERR_CUDA;
+  };
+  *steps = 0;
+  double f0 = 0;
+  vx_status st = residual(&f0);
+  if (st != VX_OK) return st;
+  for (int k = 0; k < max_steps && f0 >= tol && f0 == f0; ++k) {
+    AdjOut o = {};
+    st = saved == VX_F64 ? plain_solve<PolF64>(t, X, prm, F, nullptr, false, 1e-4, 5000, 20, &o, s)
+                         : plain_solve<PolF32>(t, X, prm, F, nullptr, false, 1e-4, 5000, 20, &o, s);
+    if (st != VX_OK) return st;
+    if (o.status != VX_OK) break;          // negative curvature or no convergence
+    k_nt_step<<<nb, kT, 0, s>>>(V, X, plain_ws(t).x, backup);
+    double f1 = 0;
+    st = residual(&f1);
+    if (st != VX_OK) return st;
+    if (!(f1 < f0)) {                      // not an improvement: undo
+      cudaError_t e = cudaMemcpyAsync(X, backup, 16 * (size_t)V, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return VX_ERR_CUDA;
+      break;
+    }
+    f0 = f1;
+    ++*steps;
+  }
+  *fmax = f0;
+  return VX_OK;
+}
+
 vx_status adjoint_plain(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, const AdjParams& ap,
                         int check_every, AdjOut* out, cudaStream_t s) {
   return t->dtype == VX_F64

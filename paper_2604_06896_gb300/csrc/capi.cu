@@ -446,8 +446,15 @@ vx_status vx_minimize(vx_tissue t, double* X, const vx_params* p, const vx_min_o
                              as_stream(stream));
   if (s != VX_OK) return s;
   if (refine && out.status == VX_OK && out.iters < o->max_iter) {
-    // FP64 arithmetic from the FP32 result (X is FP64 in and out; the
-    // tissue's buffers hold either precision)
+    // Newton steps (FP64 residuals, CG on the Hessian), then FP64 FIRE from
+    // there to tol: the FIRE stage checks the T1 rule and the stop rule at
+    // its first iteration and ends at once when the Newton steps reached
+    // tol (X is FP64 in and out; the tissue's buffers hold either precision)
+    int nsteps = 0;
+    double fm = 0.0;
+    s = vx::newton_refine(t, X, prm, o->tol, 8, &nsteps, &fm, as_stream(stream));
+    if (s != VX_OK) return s;
+    out.force_evals += 2 * nsteps + 1;
     const vx::MinOut first = out;
     vx::MinParams mp2 = to_min_params(o);
     mp2.max_iter = o->max_iter - first.iters;

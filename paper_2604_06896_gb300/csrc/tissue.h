@@ -102,6 +102,13 @@ vx_status sensitivity(vx_tissue_s* t, const double* Xstar, const ParamsD& prm, c
                       int count, const int32_t* kind, const int32_t* index, bool minres,
                       double rtol, int max_iter, int check_every, double* out, int32_t* status,
                       cudaStream_t s);
+// Newton steps X += H^-1 F towards force balance from a near-equilibrium:
+// F in FP64 arithmetic, H^-1 F by the plain-path CG on the tissue's
+// Hessian-vector product.  Stops at max|F| < tol, after max_steps, at a
+// step that does not lower max|F| (undone), or when CG meets negative
+// curvature.  *steps: accepted steps; *fmax: max|F| at the returned X.
+vx_status newton_refine(vx_tissue_s* t, double* X, const ParamsD& prm, double tol,
+                        int max_steps, int* steps, double* fmax, cudaStream_t s);
 size_t aniso_scratch_doubles(int n);
 vx_status aniso_cost_view(const View<PolF64>& v, const double* q_target, double* gradX,
                           double* scratch, double* C, cudaStream_t s);
