@@ -297,7 +297,8 @@ def c4_oracle_errors(check):
                     "pipeline is measured by tests/test_gpu_c4.py"}
 
 
-def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, compare=True):
+def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, compare=True,
+                           dist=None):
     """The batched forward workload: 512 periodic Voronoi tissues of
     log-uniform size in [200, 5000] cells (7.5e5 cells in all), per-tissue
     p0 ~ U(3.5, 4.0), per-edge Lambda ~ U(0, 0.1), FP32, FIRE + T1 to
@@ -306,7 +307,10 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, c
     (L2 flushed before each timed step).  The plain GPU path (one launch per
     sub-step, one tissue at a time) is too slow for the whole batch; it is
     compared with the batched path on every subset_every-th tissue (the same
-    inputs and options for both)."""
+    inputs and options for both).  With a process group of N ranks the
+    tissues are dealt by LPT (shard.lpt_shards), each rank relaxes its share
+    as one batch on its GPU, and the value is the evaluations of all ranks
+    over the slowest rank's time (no collective inside the timed region)."""
     batch = vi.batch_c3()
     meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
     kw = dict(tol=1e-6, max_iter=max_iter, dt0=0.01, dt_max=0.5, l_min=5e-3)
@@ -337,6 +341,18 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, c
         return evals / (ms * 1e-3), ms / nsteps, rs
 
     allidx = list(range(len(batch)))
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    if world > 1:
+        from paper_2604_06896_gb300 import shard
+        mine = shard.lpt_shards([c["n"] for c in batch], world)[dist.get_rank()]
+        value, ms_step, rs = run_batched(mine, steps)
+        t = torch.tensor([ms_step, value * ms_step * 1e-3], dtype=torch.float64, device="cuda")
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        ev = t[1:].clone()
+        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+        return {"metric": "vertex-force evals/s", "value": ev.item() / (mx.item() * 1e-3),
+                "ms_per_step": mx.item(), "ranks": world, "sharding": "LPT by cell count"}
     value, ms_step, rs = run_batched(allidx, steps)
     if not compare:
         return {"metric": "vertex-force evals/s", "value": value, "ms_per_step": ms_step,
@@ -647,8 +663,10 @@ def run_gpu(args):
     grad, grad_check = grad_metric(vx, torch, steps=max(1, args.steps), warmup=1)
     bulk = None if args.no_batch else bulk_forces_metric(vx, torch, peak, n=args.bulk_cells,
                                                          steps=args.bulk_steps)
-    batched = None if args.no_batch else batched_forward_metric(vx, torch, steps=1)
-    batched_grad = None if args.no_batch else batched_gradient_metric(vx, torch)
+    batched = None if args.no_batch else batched_forward_metric(
+        vx, torch, steps=1, dist=dist if world > 1 else None)
+    # one GPU only: the c5 line compares with the plain path tissue by tissue
+    batched_grad = None if args.no_batch or world > 1 else batched_gradient_metric(vx, torch)
 
     # cpu_baseline leg: the oracle timed on the host cores, and the oracle
     # checked against this run's results
