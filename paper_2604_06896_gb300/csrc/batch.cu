@@ -103,6 +103,12 @@ struct BatchArgs {
   const double *KA, *KP, *A0, *P0, *lam;  // per cell / per edge or null
   MinParams mp;
   MinOut* out;
+  // a second queue (the cluster kernel's) that k_min_batch takes tissues
+  // from once its own is empty, so that no SM idles while large tissues
+  // remain; null: none
+  int* counter2;
+  const int* order2;
+  int count2;
 };
 
 // The flat-table pointers of tissue d (global memory).
@@ -152,14 +158,27 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int item;
   __shared__ double gslots[3][4 * (T / 32 + 1)];
+  __shared__ int from2;
   const int tid = threadIdx.x;
+  bool second = false;
   for (;;) {
-    if (tid == 0) item = atomicAdd(g.counter, 1);
+    if (tid == 0) {
+      int q = second ? atomicAdd(g.counter2, 1) : atomicAdd(g.counter, 1);
+      if (!second && q >= g.count && g.counter2) {
+        second = true;
+        q = atomicAdd(g.counter2, 1);
+      }
+      item = q;
+      from2 = second ? 1 : 0;
+    }
     __syncthreads();
     const int k = item;
+    const bool q2 = from2 != 0;
+    second = q2;
     __syncthreads();
-    if (k >= g.count) break;
-    const BatchDesc d = g.desc[g.order[k]];
+    if (k >= (q2 ? g.count2 : g.count)) break;
+    const int tk = q2 ? g.order2[k] : g.order[k];
+    const BatchDesc d = g.desc[tk];
     ParamsD prm;
     prm.KA = g.KA ? g.KA + d.cbase : nullptr;
     prm.KP = g.KP ? g.KP + d.cbase : nullptr;
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
       for (int e = tid; e < d.E; e += T) lam[e] = (R)prm.la(e);
       __syncthreads();
       min_body_mem<P, T>(v, cell, vel, frc, lam, sb, tb, sl, prm, g.mp, Xin, Xo,
-                         g.out + g.order[k]);
+                         g.out + tk);
       __syncthreads();
       for (int h = tid; h < d.HE; h += T) {
         gt[h] = v.tgt[h];
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(T) k_min_batch(BatchArgs g) {
       Slots sl = {gslots[0], gslots[1], gslots[2]};
       min_body_mem<P, T>(v, slice16<R2>(g.cellc, d.cbase), slice16<R2>(g.vel, d.vbase), slice16<R2>(g.frc, d.vbase),
                          prm.lam, g.shortbits + d.sbase, g.touched + d.tbase, sl, prm, g.mp, Xin,
-                         Xo, g.out + g.order[k]);
+                         Xo, g.out + tk);
     }
     __syncthreads();
   }
@@ -1331,7 +1350,7 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
     ccfg.gridDim = dim3(vx::kMcNR * gc, 1, 1);
   }
   const int sm_left = std::max(1, sms - gc * vx::kMcNR);
-  const int grid = rest.empty() ? 0 : std::max(1, std::min((int)rest.size(), occ * sm_left));
+  const int grid = rest.empty() ? 0 : std::max(1, std::min((int)rest.size() + m, occ * sm_left));
   vx::BatchArgs a = make_batch_args(b, X, p, mp);
   vx::BatchArgs al = a;   // the cluster kernel's queue
   al.order = b->d_order2;
@@ -1339,6 +1358,11 @@ vx_status run_batch(vx_batch b, double* X, const vx_batch_params* p, const vx::M
   al.counter = b->d_counter + 1;
   a.order = b->d_order2 + m;
   a.count = (int)rest.size();
+  if (m > 0) {  // the CTA kernel helps with the large tissues when done
+    a.counter2 = b->d_counter + 1;
+    a.order2 = b->d_order2;
+    a.count2 = m;
+  }
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 8, s);
     if (e != cudaSuccess) return e;
