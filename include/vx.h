@@ -459,11 +459,15 @@ vx_status vx_batch_topology(vx_batch b, int32_t* he, int32_t* face_he, int32_t* 
 /*
  * vx_minimize_batched — vx_minimize for every tissue of the batch in one
  * persistent launch (replayed from a CUDA graph captured at the first call
- * with these arguments).  CTAs take tissues largest first; a tissue whose
- * working set fits the CTA's shared-memory allocation is solved there, a
- * larger one from L2-resident global memory.  X dev float64 [sum V][2]
- * in/out; r host [count] (out).  opts->path and check_every are ignored.
- * Synchronises `stream`.
+ * with these arguments).  Tissues whose working set fits a CTA's
+ * shared-memory allocation are solved there, one CTA each, taken largest
+ * first; larger ones (up to 6,144 cells) by 8-CTA thread-block clusters from
+ * L2-resident global memory, on a share of the SMs proportional to their
+ * cells, in a second launch that runs beside the first; the CTA launch
+ * takes tissues from the clusters' queue once its own is empty (a tissue
+ * above 6,144 cells is solved by one CTA from L2).  X dev float64
+ * [sum V][2] in/out; r host [count] (out).  opts->path and check_every are
+ * ignored.  Synchronises `stream`.
  */
 vx_status vx_minimize_batched(vx_batch b, double* X, const vx_batch_params* p,
                               const vx_min_opts* o, vx_min_result* r, void* stream);
