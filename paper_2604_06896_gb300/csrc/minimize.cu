@@ -130,9 +130,9 @@ __global__ void k_t1(View<P> v, ParamsD prm, double lmin, uint32_t* shortbits, u
   if (ctrl->done || !ctrl->any_short) return;
   if (threadIdx.x == 0) n_dirty = 0;
   __syncthreads();
-  if (threadIdx.x < 32) {
+  {
     T1Stats st = {0, 0, 0};
-    t1_pass_warp(v, prm, lmin, shortbits, touched, &st, dirty, CAP, &n_dirty, events);
+    t1_pass_block(v, prm, lmin, shortbits, touched, &st, dirty, CAP, &n_dirty, events);
     if (threadIdx.x == 0) {
       ctrl->n_t1 += st.n_t1;
       ctrl->n_stretch += st.n_stretch;

@@ -19,7 +19,9 @@ template <class P>
 vx_status minimize_plain_t(vx_tissue_s* t, double* X, const ParamsD& prm, const MinParams& mp,
                            int check_every, MinOut* out_h, cudaStream_t s);
 
-constexpr int kSmemMax = 227 * 1024;
+// dynamic shared memory of a resident tissue: 227 KiB per CTA less room for
+// the kernels' static shared memory (the T1 pass keeps its candidates there)
+constexpr int kSmemMax = 224 * 1024;
 constexpr int kClusterT = 256;  // 255 registers per thread: no spills
 constexpr int kClusterNR = 16;
 // Cells one T1 pass may change before the team falls back to a full cell

@@ -260,16 +260,18 @@ __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P:
     if (mp.l_min > 0) {
       if (tm.sync_or(fl, sl.b)) {
         bool ovf = false;
-        if (tm.rank() == 0 && threadIdx.x < 32) {
+        if (tm.rank() == 0) {
           T1Stats s1 = {0, 0, 0};
           int nd = 0;
-          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1, sl.dirty, sl.dirty_cap,
-                       sl.dirty ? &nd : nullptr, mp.edge_events);
+          t1_pass_block(vw, prm, mp.l_min, shortbits, touched, &s1, sl.dirty, sl.dirty_cap,
+                        sl.dirty ? &nd : nullptr, mp.edge_events);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
-          nd = __shfl_sync(0xffffffffu, nd, 0);
-          ovf = !sl.dirty || nd > sl.dirty_cap;
-          if (!ovf) refresh_cells(vw, cell, prm, sl.dirty, nd);
+          if (threadIdx.x < 32) {
+            nd = __shfl_sync(0xffffffffu, nd, 0);
+            ovf = !sl.dirty || nd > sl.dirty_cap;
+            if (!ovf) refresh_cells(vw, cell, prm, sl.dirty, nd);
+          }
         }
         const bool full = tm.sync_or(ovf, sl.c);
         // The moved vertices restart from rest.  The 32 vertices of a mask
@@ -943,10 +945,10 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     const bool fl = cell_pass(lminR);
     if (mp.l_min > 0) {
       if (__syncthreads_or(fl)) {
-        if (tid < 32) {
+        {
           T1Stats s1 = {0, 0, 0};
-          t1_pass_warp(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, nullptr,
-                       mp.edge_events);
+          t1_pass_block(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, nullptr,
+                        mp.edge_events);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
         }

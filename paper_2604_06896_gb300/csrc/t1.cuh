@@ -373,3 +373,130 @@ __device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double 
 }
 
 }  // namespace vx
+
+namespace vx {
+
+// The T1 pass by all warps of one CTA, with the same result as
+// t1_pass_warp: each round, the next (up to) eight flagged edges in id
+// order are evaluated at once, one warp each, against the current tissue;
+// warp 0 then commits them in id order.  A candidate's evaluation reads
+// only the four cells around its edge (their corners, half-edges and
+// parameters), and a commit changes only the four cells around its own
+// edge, so the evaluation of a later candidate whose cells are disjoint
+// from every cell committed before it in the round is the one the
+// sequential pass would make.  The round stops at the first candidate that
+// fails this test, at a candidate that a join (an edge made short by a
+// commit, with a larger id than the committed edge) precedes, and at a
+// candidate found no longer short after an earlier commit of the round
+// (its cells are not known); the next round starts there.  Every thread of
+// the CTA must call it.
+template <class P>
+__device__ __noinline__ void t1_pass_block(View<P> v, const ParamsD& prm, double lmin,
+                                           uint32_t* shortbits, uint32_t* touched, T1Stats* st,
+                                           int* dirty = nullptr, int dirty_cap = 0,
+                                           int* n_dirty = nullptr, int* events = nullptr) {
+  constexpr int kNW = 8;
+  __shared__ T1Cand<P> slot[kNW];
+  __shared__ int cand[kNW], okv[kNW], rcells[4 * kNW];
+  __shared__ int ncand, s_cursor;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5) < kNW ? (int)(blockDim.x >> 5) : kNW;
+  const int nwords = (v.E + 31) >> 5;
+  if (threadIdx.x == 0) s_cursor = 0;
+  __syncthreads();
+  for (;;) {
+    // the next flagged edges at or after the cursor, in id order
+    if (warp == 0) {
+      const int cursor = s_cursor;
+      int count = 0;
+      for (int w0 = cursor >> 5; w0 < nwords && count < nw; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t bits = w < nwords ? ((volatile const uint32_t*)shortbits)[w] : 0u;
+        if (w == (cursor >> 5)) bits &= ~((1u << (cursor & 31)) - 1u);
+        unsigned nz = __ballot_sync(0xffffffffu, bits != 0);
+        while (nz && count < nw) {
+          const int src = __ffs(nz) - 1;
+          nz &= nz - 1;
+          uint32_t b = __shfl_sync(0xffffffffu, bits, src);
+          while (b && count < nw) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            if (lane == 0) cand[count] = ((w0 + src) << 5) + bit;
+            ++count;
+          }
+        }
+      }
+      if (lane == 0) ncand = count;
+    }
+    __syncthreads();
+    const int k = ncand;
+    if (k == 0) break;
+    if (warp < k) {
+      T1Cand<P> c;
+      const bool r = t1_evaluate(v, prm, lmin, cand[warp], c);
+      if (lane == 0) {
+        slot[warp] = c;
+        okv[warp] = r ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int nr = 0, minjoin = 0x7fffffff, next = s_cursor;
+      for (int j = 0; j < k; ++j) {
+        const int e = cand[j];
+        if (j > 0) {
+          if (minjoin < e) break;
+          if (!okv[j] && nr > 0) break;
+          bool conflict = false;
+          if (okv[j])
+            for (int q = 0; q < 4 && !conflict; ++q)
+              for (int r = 0; r < nr; ++r)
+                if (slot[j].C[q] == rcells[r]) {
+                  conflict = true;
+                  break;
+                }
+          if (conflict) break;
+        }
+        if (lane == 0) atomicAnd(&shortbits[e >> 5], ~(1u << (e & 31)));
+        next = e + 1;
+        __syncwarp();
+        if (!okv[j]) continue;
+        const T1Cand<P> c = slot[j];
+        const bool take_t1 = c.allow && c.Et < c.Es;
+        if (lane == 0 && events) events[2 * e + (take_t1 ? 1 : 0)] += 1;
+        t1_commit(v, c, take_t1, touched);
+        if (lane == 0) {
+          if (take_t1) st->n_t1++;
+          else st->n_stretch++;
+          if (n_dirty) {
+            for (int q = 0; q < 4; ++q) {
+              if (*n_dirty < dirty_cap) dirty[*n_dirty] = c.C[q];
+              ++*n_dirty;
+            }
+          }
+          for (int q = 0; q < 4; ++q) rcells[nr + q] = c.C[q];
+        }
+        nr += 4;
+        __syncwarp();
+        // edges at a or b with a larger id that are now short join the pass
+        int join = 0x7fffffff;
+        if (lane < 6) {
+          const int vv = lane < 3 ? c.a : c.b;
+          const int hh = v.vout[(lane % 3) * v.V + vv];
+          const int f = hh >> 1;
+          if (f > e && edge_len_p(v, hh) < lmin) {
+            atomicOr(&shortbits[f >> 5], 1u << (f & 31));
+            join = f;
+          }
+        }
+        join = __reduce_min_sync(0xffffffffu, join);
+        if (join < minjoin) minjoin = join;
+        __syncwarp();
+      }
+      if (lane == 0) s_cursor = next;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace vx
