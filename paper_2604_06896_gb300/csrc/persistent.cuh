@@ -187,6 +187,23 @@ __device__ __noinline__ void refresh_cells(View<P> vw, R2* cell, const ParamsD& 
   }
 }
 
+// The same for the whole CTA (out of line: the array-state loop keeps its
+// registers).
+template <class P, class R2>
+__device__ __noinline__ void refresh_cells_cta(View<P> vw, R2* cell, const ParamsD& prm,
+                                               const int* list, int count) {
+  using R = typename P::R;
+  for (int q = (int)threadIdx.x; q < count; q += (int)blockDim.x) {
+    const int c = list[q];
+    R A, Pp;
+    cell_geometry(vw, c, A, Pp, (R)0, (uint32_t*)nullptr);
+    R2 cc;
+    cc.x = (R)2 * (R)prm.ka(c) * (A - (R)prm.a0(c));
+    cc.y = (R)2 * (R)prm.kp(c) * (Pp - (R)prm.p0(c));
+    cell[c] = cc;
+  }
+}
+
 template <class P, class Team, int MAXC, class LamT>
 __device__ void min_body(const Team& tm, View<P> vw, typename Vec2Of<typename P::R>::T* cell,
                          const LamT* lam, uint32_t* shortbits, uint32_t* touched, Slots sl,
@@ -945,14 +962,22 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
     const bool fl = cell_pass(lminR);
     if (mp.l_min > 0) {
       if (__syncthreads_or(fl)) {
+        // cells the pass changed (shared memory); their coefficients are
+        // recomputed by the whole CTA, or every cell's if the list overflows
+        constexpr int kMemDirty = 512;
+        __shared__ int mdirty[kMemDirty];
+        __shared__ int mnd;
         {
           T1Stats s1 = {0, 0, 0};
-          t1_pass_block(vw, prm, mp.l_min, shortbits, touched, &s1, nullptr, 0, nullptr,
+          int nd = 0;
+          t1_pass_block(vw, prm, mp.l_min, shortbits, touched, &s1, mdirty, kMemDirty, &nd,
                         mp.edge_events);
           n_t1 += s1.n_t1;
           n_st += s1.n_stretch;
+          if (tid == 0) mnd = nd;
         }
         __syncthreads();
+        const int nd = mnd;
         for (int w = tid; w < (V + 31) / 32; w += T) {
           uint32_t b = touched[w];
           touched[w] = 0;
@@ -965,7 +990,11 @@ __device__ void min_body_mem(View<P> vw, typename Vec2Of<typename P::R>::T* cell
             vel[i] = z;
           }
         }
-        cell_pass((R)0);
+        if (nd > kMemDirty) {
+          cell_pass((R)0);
+        } else {
+          refresh_cells_cta(vw, cell, prm, mdirty, nd);
+        }
         __syncthreads();
       }
     } else {
