@@ -132,38 +132,66 @@ def cpu_sample(seconds=12.0):
                        f"p0=3.7 tissue from its Voronoi state, numpy FP64, {dt:.1f} s")
 
 
-def _oracle_worker(job):
-    """One host process of the all-cores oracle sample: FIRE + T1 on the
-    10,000-cell tissue (p0 = job's), for about `seconds`."""
-    p0, seconds = job
+_ORACLE_WORKER = {}
+
+
+def _oracle_init(counter):
+    """Pool initializer: each host process takes the next p0 of the sweep
+    and builds the oracle's mesh of that tissue once."""
     from oracle import mesh as omesh
+    with counter.get_lock():
+        idx = counter.value
+        counter.value += 1
+    c = vi.tissue_c2(vi.C2_P0_SWEEP[idx % 3])
+    _ORACLE_WORKER["tissue"] = (c, omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"]))
+
+
+def _oracle_worker(seconds):
+    """One host process of the all-cores oracle sample: FIRE + T1 on its
+    10,000-cell tissue from the Voronoi state for about `seconds` (at least
+    one iteration; the time per iteration is calibrated once per process)."""
     from oracle import solvers as osolv
-    c = vi.tissue_c2(p0)
-    t = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    c, t = _ORACLE_WORKER["tissue"]
     p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
     o = opts_for(c["A0"], 0)
-    mo = osolv.MinOpts(tol=o["tol"], max_iter=3, dt0=o["dt0"], dt_max=o["dt_max"])
-    t0 = time.perf_counter()
-    r = osolv.relax(t["vert"], t, p, mo, l_min=o["l_min"])
-    per = (time.perf_counter() - t0) / (r.iters + 1)
-    mo.max_iter = max(3, int(seconds / per))
+    mo = osolv.MinOpts(tol=o["tol"], max_iter=2, dt0=o["dt0"], dt_max=o["dt_max"])
+    if "per" not in _ORACLE_WORKER:
+        t0 = time.perf_counter()
+        r = osolv.relax(t["vert"], t, p, mo, l_min=o["l_min"])
+        _ORACLE_WORKER["per"] = (time.perf_counter() - t0) / (r.iters + 1)
+    mo.max_iter = max(1, int(seconds / _ORACLE_WORKER["per"]))
     t0 = time.perf_counter()
     r = osolv.relax(t["vert"], t, p, mo, l_min=o["l_min"])
     return t["vert"].shape[0], r.iters + 1, time.perf_counter() - t0
 
 
-def cpu_sample_all_cores(seconds=15.0):
-    """The oracle on every host core at once: one process per core, each
-    relaxing the 10,000-cell tissue (the three p0 in turn) for about
-    `seconds`; value = sum of V x force evaluations / the longest process
-    time.  Processes are spawned (none is forked from a CUDA process)."""
+def oracle_pool():
+    """One spawned host process per core, each holding its tissue."""
     import multiprocessing as mp
-    cores = os.cpu_count() or 1
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    jobs = [(vi.C2_P0_SWEEP[k % 3], seconds) for k in range(cores)]
-    with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_worker, jobs)
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    return ctx.Pool(cores, initializer=_oracle_init, initargs=(ctx.Value("i", 0),)), cores
+
+
+def cpu_sample_all_cores(seconds=15.0, pool=None):
+    """The oracle on every host core at once: one process per core, each
+    relaxing the 10,000-cell tissue of one p0 (3.5, 3.7, 3.9 in turn) for
+    about `seconds`; value = sum of V x force evaluations / the longest
+    process time.  Processes are spawned (none is forked from a CUDA
+    process)."""
+    own = pool is None
+    if own:
+        pool, cores = oracle_pool()
+    else:
+        cores = pool._processes
+    try:
+        res = pool.map(_oracle_worker, [seconds] * cores, chunksize=1)
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     evals = sum(v * e for v, e, _ in res)
     wall = max(d for _, _, d in res)
     return dict(value=evals / wall, unit=UNIT, cores=cores, kind="oracle",
@@ -177,14 +205,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        pass
-    vals = []
-    t_all = time.perf_counter()
-    for _ in range(args.steps):
-        s = cpu_sample_all_cores(seconds=max(5.0, 40.0 / max(1, args.steps)))
-        vals.append(s["value"])
-    wall = time.perf_counter() - t_all
+    per_step = max(3.0, 40.0 / max(1, args.steps))
+    pool, _ = oracle_pool()
+    with pool:
+        for _ in range(args.warmup):
+            cpu_sample_all_cores(seconds=1.0, pool=pool)
+        vals = []
+        t_all = time.perf_counter()
+        for _ in range(args.steps):
+            s = cpu_sample_all_cores(seconds=per_step, pool=pool)
+            vals.append(s["value"])
+        wall = time.perf_counter() - t_all
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
