@@ -423,7 +423,7 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, c
                        "vs_plain_gpu_path": sub_value / plain_value}}
 
 
-def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None):
+def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None, compare=True):
     """The batched inverse-design workload: 64 periodic Voronoi tissues of
     10,000 cells (box 100, A0 = 1 per cell, Lambda ~ U(0, 0.1) per edge,
     p0 = 3.7), FP32; one equilibrium-gradient solve = the free relaxation
@@ -456,6 +456,10 @@ def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None):
     e1.synchronize()
     ms_b = e0.elapsed_time(e1)
     b.close()
+    if not compare:
+        return {"metric": "equilibrium-gradient solves/s", "value": len(batch) / (ms_b * 1e-3),
+                "ms_per_batch": ms_b,
+                "cg_iters": [int(min(r[1].cg_iters for r in rs)), int(max(r[1].cg_iters for r in rs))]}
     idx = list(range(len(batch))) if plain_tissues is None else list(range(plain_tissues))
     ms_p = 0.0
     for k in idx:
@@ -843,6 +847,9 @@ def main():
     ap.add_argument("--bulk-only", action="store_true",
                     help="only the bulk energy + force line (for ncu)")
     ap.add_argument("--bulk-cells", type=int, default=1_000_000)
+    ap.add_argument("--c5-only", action="store_true",
+                    help="only the batched gradient workload, without the plain-path comparison "
+                         "(for a launch list)")
     ap.add_argument("--c3-only", action="store_true",
                     help="only the batched forward workload, without the plain-path comparison "
                          "(for a launch list)")
@@ -856,6 +863,10 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.c5_only:
+        import torch
+        import paper_2604_06896_gb300 as vx
+        print(json.dumps(batched_gradient_metric(vx, torch, compare=False)))
     elif args.c3_only:
         import torch
         import paper_2604_06896_gb300 as vx
