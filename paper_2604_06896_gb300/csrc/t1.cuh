@@ -298,88 +298,15 @@ __device__ __forceinline__ void t1_commit(const View<P>& v, const T1Cand<P>& k, 
   __syncwarp();
 }
 
-// The T1 pass by the 32 lanes of one warp: edges flagged in `shortbits` in
-// increasing id (the mask is scanned 128 words per coalesced warp load and
-// only non-zero words are visited; once a join has set a bit further on in
-// the chunk, the rest of it is read word by word).  Clears `shortbits`.
-// Cells whose geometry changed are appended to `dirty` (up to `dirty_cap`;
-// `*n_dirty` may exceed it).  `events` (optional, [E][2]) counts the
-// stretches and T1s of every edge.  Every lane must call it.
-template <class P>
-__device__ __noinline__ void t1_pass_warp(View<P> v, const ParamsD& prm, double lmin,
-                                          uint32_t* shortbits, uint32_t* touched, T1Stats* st,
-                                          int* dirty = nullptr, int dirty_cap = 0,
-                                          int* n_dirty = nullptr, int* events = nullptr) {
-  const int lane = threadIdx.x & 31;
-  const int nwords = (v.E + 31) >> 5;
-  for (int w0 = 0; w0 < nwords; w0 += 128) {
-    uint32_t any = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = w0 + 4 * lane + q;
-      // generic loads: the mask lives in shared memory on the resident
-      // path and in global memory on the team paths
-      any |= idx < nwords ? ((volatile const uint32_t*)shortbits)[idx] : 0u;
-    }
-    const unsigned nz = __ballot_sync(0xffffffffu, any != 0);
-    bool joined = false;
-    const int wend = w0 + 128 < nwords ? w0 + 128 : nwords;
-    for (int w = w0; w < wend; ++w) {
-      if (!joined && !((nz >> ((w - w0) >> 2)) & 1u)) {
-        w |= 3;  // skip the rest of this lane's group of four words
-        continue;
-      }
-      for (;;) {
-        __syncwarp();
-        const uint32_t bits = ((volatile const uint32_t*)shortbits)[w];
-        if (!bits) break;
-        const int bit = __ffs(bits) - 1;
-        __syncwarp();
-        if (lane == 0) shortbits[w] = bits & (bits - 1);
-        __syncwarp();
-        const int e = (w << 5) + bit;
-        T1Cand<P> k;
-        if (!t1_evaluate(v, prm, lmin, e, k)) continue;
-        const bool take_t1 = k.allow && k.Et < k.Es;
-        if (lane == 0 && events) events[2 * e + (take_t1 ? 1 : 0)] += 1;
-        t1_commit(v, k, take_t1, touched);
-        if (lane == 0) {
-          if (take_t1) st->n_t1++;
-          else st->n_stretch++;
-          if (n_dirty) {
-            for (int q = 0; q < 4; ++q) {
-              if (*n_dirty < dirty_cap) dirty[*n_dirty] = k.C[q];
-              ++*n_dirty;
-            }
-          }
-        }
-        __syncwarp();
-        // Edges at a or b with a larger id that are now short join this pass.
-        bool join = false;
-        if (lane < 6) {
-          const int vv = lane < 3 ? k.a : k.b;
-          const int hh = v.vout[(lane % 3) * v.V + vv];
-          const int f = hh >> 1;
-          if (f > e && edge_len_p(v, hh) < lmin) {
-            atomicOr(&shortbits[f >> 5], 1u << (f & 31));
-            join = true;
-          }
-        }
-        joined |= __any_sync(0xffffffffu, join);
-      }
-    }
-  }
-  __syncwarp();
-}
-
-}  // namespace vx
-
-namespace vx {
-
-// The T1 pass by all warps of one CTA, with the same result as
-// t1_pass_warp: each round, the next (up to) eight flagged edges in id
-// order are evaluated at once, one warp each, against the current tissue;
-// warp 0 then commits them in id order.  A candidate's evaluation reads
+// The T1 pass over the edges flagged in `shortbits`, by all warps of one
+// CTA, with the result of taking the flagged edges one at a time in
+// increasing id (edges with a larger id that a commit makes short join the
+// pass; `shortbits` ends cleared; cells whose geometry changed are appended
+// to `dirty`, up to `dirty_cap`, while `*n_dirty` counts them all; `events`,
+// optional [E][2], counts each edge's stretches and T1s).  Each round, the
+// next (up to) eight flagged edges in id order are evaluated at once, one
+// warp each, against the current tissue; warp 0 then commits them in id
+// order.  A candidate's evaluation reads
 // only the four cells around its edge (their corners, half-edges and
 // parameters), and a commit changes only the four cells around its own
 // edge, so the evaluation of a later candidate whose cells are disjoint
