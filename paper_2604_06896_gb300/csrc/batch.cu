@@ -701,7 +701,7 @@ template <class P, int NR, int MAXC>
 __global__ void __launch_bounds__(kGcT) k_grad_cluster(BatchGradArgs a) {
   using Team = ClusterTeam<kGcT, NR>;
   __shared__ int item;
-  __shared__ double slots[3][4 * (kGcT / 32 + 1 + NR)];
+  __shared__ double slots[3][4 * (kGcT / 32 + 2)];
   __shared__ int dirty[kGcDirty];
   const BatchArgs& g = a.b;
   Team tm;
@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(kMcT) k_min_cluster_batch(BatchArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
   using Team = ClusterTeam<kMcT, kMcNR>;
   __shared__ int item;
-  __shared__ double slots[3][4 * (kMcT / 32 + 1 + kMcNR)];
+  __shared__ double slots[3][4 * (kMcT / 32 + 2)];
   __shared__ int dirty[kMcDirty];
   Team tm;
   for (;;) {

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(T) k_adj_res(PersistArgs g) {
 template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
-  __shared__ double slots[3][4 * (T / 32 + 1 + NR)];
+  __shared__ double slots[3][4 * (T / 32 + 2)];
   __shared__ int dirty[kDirtyCap];
   ClusterTeam<T, NR> tm;
   for (int w = tm.first(); w < (g.E + 31) / 32; w += tm.stride()) g.shortbits[w] = 0;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(T) k_min_cluster(PersistArgs g) {
 template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_min_cluster_many(const PersistArgs* args) {
   using R2 = typename Vec2Of<typename P::R>::T;
-  __shared__ double slots[3][4 * (T / 32 + 1 + NR)];
+  __shared__ double slots[3][4 * (T / 32 + 2)];
   __shared__ int dirty[kDirtyCap];
   const PersistArgs& g = args[blockIdx.x / NR];
   ClusterTeam<T, NR> tm;
@@ -277,7 +277,7 @@ template <class P, int T, int NR, int MAXC>
 __global__ void __launch_bounds__(T) k_adj_cluster(PersistArgs g) {
   using R2 = typename Vec2Of<typename P::R>::T;
   using R4 = typename Vec2Of<typename P::R>::T4;
-  __shared__ double slots[3][4 * (T / 32 + 1 + NR)];
+  __shared__ double slots[3][4 * (T / 32 + 2)];
   ClusterTeam<T, NR> tm;
   Slots sl = {slots[0], slots[1], slots[2]};
   adj_body<P, ClusterTeam<T, NR>, MAXC>(tm, global_view<P>(g), (R4*)g.cell, g.prm.lam,

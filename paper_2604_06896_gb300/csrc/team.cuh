@@ -123,10 +123,6 @@ struct ClusterTeam {
     reduce<NV, true>(out, slots, nmax);
   }
   // kTreeDone: v already holds warp totals (in every lane).
-  // `slots` holds (kWarps + 1 + NR) * NV doubles: the warps' totals, then
-  // one row per rank into which every CTA writes its total (distributed
-  // shared memory) before the cluster barrier; afterwards each thread sums
-  // the NR rows in rank order, so every CTA gets the same value.
   template <int NV, bool kTreeDone = false>
   __device__ __forceinline__ void reduce(double (&v)[NV], double* slots, int nmax) const {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -142,28 +138,37 @@ struct ClusterTeam {
       if (lane == 0) slots[w * NV + k] = x;
     }
     __syncthreads();
-    // the CTA's total of value k, pushed into row (kWarps + 1 + rank) of
-    // every CTA of the cluster
-    if (threadIdx.x < NV * NR) {
-      const int k = threadIdx.x % NV, q = threadIdx.x / NV;
+    // CTA total into row kWarps.
+    if (threadIdx.x < NV) {
+      const int k = threadIdx.x;
       double s = 0.0;
-      for (int i = 0; i < kWarps; ++i) {
-        const double y = slots[i * NV + k];
+      for (int q = 0; q < kWarps; ++q) {
+        const double y = slots[q * NV + k];
         s = (k >= NV - nmax) ? fmax(s, y) : s + y;
       }
-      *cg::this_cluster().map_shared_rank(&slots[(kWarps + 1 + rank()) * NV + k], q) = s;
+      slots[kWarps * NV + k] = s;
     }
     cg::this_cluster().sync();
+    // Warp 0 gathers the NR totals through distributed shared memory (lane q
+    // reads rank q) and reduces them with a fixed shuffle tree into row
+    // kWarps + 1; the other warps read that row after the CTA barrier.
+    if (w == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const bool mx = k >= NV - nmax;
-      double s = 0.0;
-      for (int r = 0; r < NR; ++r) {
-        const double y = slots[(kWarps + 1 + r) * NV + k];
-        s = mx ? fmax(s, y) : s + y;
+      for (int k = 0; k < NV; ++k) {
+        const bool mx = k >= NV - nmax;
+        double x = (lane < NR) ? *cg::this_cluster().map_shared_rank(&slots[kWarps * NV + k], lane)
+                               : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = mx ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) slots[(kWarps + 1) * NV + k] = x;
       }
-      v[k] = s;
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = slots[(kWarps + 1) * NV + k];
   }
 };
 
