@@ -6,7 +6,9 @@ forces sum to zero).  T1 rewiring is checked against the half-edge
 invariants and the tiling identity sum A = Lx Ly.  The adjoint gradient is
 checked against central finite differences of the outer cost with
 re-minimisation, equilibrium propagation against the adjoint, and the
-centred estimator's O(beta^2) error.
+centred estimator's O(beta^2) error.  The dense adjoint's indefinite branch
+(the eigen-solve MINRES is compared with) is checked by its residual, H lam
+taken as a central difference of the forces.
 """
 import math
 
@@ -161,3 +163,53 @@ def test_ep_centered_second_order(equilibrium):
     assert 2.5 < errs[0] / errs[1] < 5.5
     g_fw, _ = solvers.ep_grad(X, t, p, gradC, 0.05, o, centered=False)
     assert np.linalg.norm(g_fw["lam"] - g_adj["lam"]) / np.linalg.norm(g_adj["lam"]) < 5e-2
+
+
+# --------------------------------------------- indefinite adjoint (Methods, "Implicit differentiation")
+
+def _planted(func_name, old, new):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(solvers, func_name)))
+    assert src.count(old) == 1, f"{old!r} not found once in {func_name}"
+    ns = dict(vars(solvers))
+    exec(compile(src.replace(old, new), f"<planted {func_name}>", "exec"), ns)
+    return ns[func_name]
+
+
+def _indefinite_case():
+    """A 40-cell Voronoi state at p0 = 4.4, not relaxed: its Hessian has
+    negative eigenvalues on the translation-free subspace."""
+    c = vi.small_tissue(40, 101, p0=4.4, lam_range=(0.02, 0.1))
+    t = mesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
+    p = {k: c[k] for k in ("KA", "KP", "A0", "P0", "lam")}
+    return t, p, t["vert"]
+
+
+def _check_indefinite_solution(solve):
+    """H lam = Pi b on the translation-free subspace, with H lam taken as a
+    central difference of the forces (H = -dF/dX), which does not use the
+    assembled Hessian, and lam free of translations."""
+    t, p, X = _indefinite_case()
+    b = np.random.default_rng(102).standard_normal(X.shape)
+    lam, info = solve(X, t, p, b)
+    assert not info["pd"] and info["min_eig"] < 0
+    h = 1e-6 / np.abs(lam).max()
+    Hl = -(model.forces(X + h * lam, t, p) - model.forces(X - h * lam, t, p)) / (2 * h)
+    Pb = b - b.mean(axis=0)
+    assert np.abs(lam.mean(axis=0)).max() < 1e-12 * np.abs(lam).max()
+    assert np.linalg.norm(Hl - Pb) < 1e-6 * np.linalg.norm(Pb)
+
+
+def test_adjoint_solve_on_an_indefinite_hessian():
+    _check_indefinite_solution(solvers.adjoint_solve)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("(U.T @ rhs) / w", "(U.T @ rhs) / np.abs(w)"),
+    ("lam = U @ ((U.T @ rhs) / w)", "lam = -U @ ((U.T @ rhs) / w)"),
+    ("lam = U @ ((U.T @ rhs) / w)", "lam = U.T @ ((U @ rhs) / w)"),
+])
+def test_indefinite_planted_mistakes_are_caught(old, new):
+    with pytest.raises(AssertionError):
+        _check_indefinite_solution(_planted("adjoint_solve", old, new))
