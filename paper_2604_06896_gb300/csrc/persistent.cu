@@ -447,7 +447,7 @@ static int choose_path(vx_tissue_s* t, int path, bool adjoint) {
   if (path == VX_PATH_CLUSTER && !cluster_fits(t)) return -1;
   if (path == VX_PATH_GRID && adjoint) return cluster_fits(t) ? VX_PATH_CLUSTER : -1;
   if (path == VX_PATH_GRID && !grid_fits(t)) return -1;
-  if (path == VX_PATH_PLAIN && adjoint) return VX_PATH_CLUSTER;
+  if (path == VX_PATH_PLAIN && adjoint) return cluster_fits(t) ? VX_PATH_CLUSTER : -1;
   return path;
 }
 
