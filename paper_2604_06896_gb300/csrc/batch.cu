@@ -1011,9 +1011,10 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   size_t hoff = 0, coff = 0;
   for (int k = 0; k < count; ++k) {
     const int n = n_cells[k], HE = 6 * n, V = 2 * n, E = 3 * n;
-    if (n < 1) {
+    if (n < 1 || n > (INT32_MAX - hb) / 6) {
       delete b;
-      return fail(VX_ERR_INVALID_ARG, "every tissue needs cells");
+      return fail(VX_ERR_INVALID_ARG, n < 1 ? "every tissue needs cells"
+                                            : "the batch holds more than 2^31 half-edges");
     }
     vx_tissue t = nullptr;
     // host-only validation and internal tables via vx_tissue_create would
@@ -1134,11 +1135,18 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   b->smem_bytes = 220 * 1024;
   b->tuned = false;
   b->gexec = nullptr;
-  *out = b;
   const vx_status r = vx_batch_restore(b, stream);
-  if (r != VX_OK) return r;
-  if (cudaStreamSynchronize(s) != cudaSuccess)
-    return fail(VX_ERR_CUDA, std::string("vx_batch_create: ") + cudaGetErrorString(cudaGetLastError()));
+  if (r != VX_OK) {
+    cudaStreamSynchronize(s);
+    vx_batch_destroy(b);
+    return r;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    const std::string m = std::string("vx_batch_create: ") + cudaGetErrorString(cudaGetLastError());
+    vx_batch_destroy(b);
+    return fail(VX_ERR_CUDA, m);
+  }
+  *out = b;
   return VX_OK;
 }
 

@@ -261,20 +261,34 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
     return e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA;
   }
   cudaStream_t s = as_stream(stream);
-  VX_CUDA_TRY(cudaMemcpyAsync(t->tgt, tgt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->nxt, nxt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->face, face.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->vout, vout.data(), 12 * (size_t)V, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->tgt0, tgt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->nxt0, nxt.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->face0, face.data(), 4 * (size_t)HE, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->vout0, vout.data(), 12 * (size_t)V, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemcpyAsync(t->ffirst0, ff.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
-  VX_CUDA_TRY(cudaMemsetAsync(t->shortbits, 0, 4 * (size_t)(E / 32 + 1), s));
-  VX_CUDA_TRY(cudaMemsetAsync(t->touched, 0, 4 * (size_t)(V / 32 + 1), s));
-  VX_CUDA_TRY(vx::rebuild_flat(t, s));
-  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  auto upload = [&]() -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    auto up = [&](void* dst, const void* src, size_t b) {
+      if (r == cudaSuccess) r = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
+    };
+    up(t->tgt, tgt.data(), 4 * (size_t)HE);
+    up(t->nxt, nxt.data(), 4 * (size_t)HE);
+    up(t->face, face.data(), 4 * (size_t)HE);
+    up(t->vout, vout.data(), 12 * (size_t)V);
+    up(t->ffirst, ff.data(), 4 * (size_t)n);
+    up(t->tgt0, tgt.data(), 4 * (size_t)HE);
+    up(t->nxt0, nxt.data(), 4 * (size_t)HE);
+    up(t->face0, face.data(), 4 * (size_t)HE);
+    up(t->vout0, vout.data(), 12 * (size_t)V);
+    up(t->ffirst0, ff.data(), 4 * (size_t)n);
+    if (r == cudaSuccess) r = cudaMemsetAsync(t->shortbits, 0, 4 * (size_t)(E / 32 + 1), s);
+    if (r == cudaSuccess) r = cudaMemsetAsync(t->touched, 0, 4 * (size_t)(V / 32 + 1), s);
+    if (r == cudaSuccess) r = vx::rebuild_flat(t, s);
+    // the host tables are locals: wait for the copies before returning
+    const cudaError_t w = cudaStreamSynchronize(s);
+    return r == cudaSuccess ? w : r;
+  };
+  e = upload();
+  if (e != cudaSuccess) {
+    vx_tissue_destroy(t);
+    set_error(std::string("vx_tissue_create: upload: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA;
+  }
   *out = t;
   return VX_OK;
 }
