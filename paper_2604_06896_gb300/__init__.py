@@ -20,10 +20,13 @@ from ._capi import (VX_ADJOINT_CG, VX_ADJOINT_MINRES, VX_COST_ANISO, VX_COST_NON
                     VX_PATH_AUTO, VX_PATH_CLUSTER, VX_PATH_GRID, VX_PATH_PLAIN, VX_PATH_RESIDENT,
                     VxError)
 
-__all__ = ["vx_batch_aniso_cost", "vx_equilibrium_grad_batched", "vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_energy_forces", "vx_minimize",
-           "vx_equilibrium_grad", "vx_hessian_vector", "vx_tissue_restore", "vx_minimize_many", "Tissue",
-           "Batch", "vx_batch_create", "vx_minimize_batched", "vx_batch_autotune",
-           "vx_batch_restore", "EquilibriumFn", "VxError"]
+__all__ = ["vx_build_mesh", "vx_seed_order", "vx_tissue_create", "vx_tissue_restore", "Tissue",
+           "vx_energy_forces", "vx_energy_forces_noalloc", "vx_hessian_vector", "vx_minimize",
+           "vx_minimize_async", "vx_minimize_many", "vx_equilibrium_grad",
+           "vx_equilibrium_grad_async", "vx_sensitivity_grad", "Batch", "vx_batch_create",
+           "vx_batch_restore", "vx_minimize_batched", "vx_batch_autotune",
+           "vx_equilibrium_grad_batched", "vx_batch_grad", "vx_batch_aniso_cost",
+           "vx_grid_barrier_selftest", "vx_version", "EquilibriumFn", "VxError"]
 
 
 def _torch():
@@ -635,6 +638,55 @@ def vx_grid_barrier_selftest(ctas, absent_rank=-1, rounds=8, wait_s=0.25):
     if st not in (capi.VX_OK, capi.VX_ERR_TIMEOUT):
         capi.check(st, "vx_grid_barrier_selftest")
     return st, out
+
+
+def _dev_tensor(name, x, dtype, shape):
+    torch = _torch()
+    if not torch.is_tensor(x) or not x.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor (the caller's device memory)")
+    if x.dtype != dtype or not x.is_contiguous() or tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {x.dtype} {tuple(x.shape)}")
+    return x
+
+
+def vx_energy_forces_noalloc(he, face_he, edge_id, Lx, Ly, X, params, F=None, E=None,
+                             status=None):
+    """vx_energy_forces without a vx_tissue and without any allocation by the
+    library (see vx.h).  he int32 [6n, 8], face_he int32 [n], edge_id int32
+    [6n] and X float64 [2n, 2] are CUDA tensors the caller owns; F float64
+    [2n, 2], E float64 [1] and status int32 [1] are CUDA outputs (F and E may
+    be None).  Asynchronous on torch's current stream: status (table checks,
+    see vx.h) is written by the GPU.  Per-cell or per-edge parameters are
+    passed as CUDA float64 tensors of n or 3n values."""
+    torch = _torch()
+    if not torch.is_tensor(face_he):
+        raise ValueError("face_he: expected a CUDA tensor (the caller's device memory)")
+    n = int(face_he.shape[0])
+    _dev_tensor("face_he", face_he, torch.int32, (n,))
+    _dev_tensor("he", he, torch.int32, (6 * n, 8))
+    _dev_tensor("edge_id", edge_id, torch.int32, (6 * n,))
+    _dev_tensor("X", X, torch.float64, (2 * n, 2))
+    if F is not None:
+        _dev_tensor("F", F, torch.float64, (2 * n, 2))
+    if E is not None:
+        _dev_tensor("E", E, torch.float64, (1,))
+    if status is None:
+        raise ValueError("status: an int32 [1] CUDA tensor is required")
+    _dev_tensor("status", status, torch.int32, (1,))
+    for k in ("KA", "KP", "A0", "P0", "lam"):
+        v = params[k]
+        if torch.is_tensor(v) and v.dim() > 0:
+            _dev_tensor(k, v, torch.float64, (3 * n,) if k == "lam" else (n,))
+    prm, keep = make_params(params, n, 3 * n)
+    st = capi.vx_energy_forces_noalloc(he.data_ptr(), face_he.data_ptr(), edge_id.data_ptr(), n,
+                                       float(Lx), float(Ly), X.data_ptr(), C.byref(prm), _ptr(F),
+                                       _ptr(E), status.data_ptr(), _stream())
+    capi.check(st, "vx_energy_forces_noalloc")
+
+
+def vx_version():
+    return capi.vx_version().decode()
 
 
 def vx_batch_autotune(b: Batch, X, params, probe_iters=200, **opts):

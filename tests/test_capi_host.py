@@ -1,5 +1,6 @@
 """C ABI without a GPU: the library loads, exports every symbol vx.h
-declares, validates arguments, and its host mesh builder reproduces the
+declares (and the Python binding offers each under the same name),
+validates arguments, and its host mesh builder reproduces the
 oracle's topology bit for bit."""
 import os
 import re
@@ -29,6 +30,34 @@ def test_exports_every_declared_symbol(vx):
         assert hasattr(_capi.lib, name), name
     assert declared == set(_capi.EXPORTED)
     assert _capi.vx_version().decode().startswith("vx ")
+
+
+# Entry points whose Python form is a method or a helper of the handle
+# classes (Tissue, Batch) or a defaults filler used by the option builders.
+_HANDLE_LEVEL = {"vx_last_error", "vx_tissue_destroy", "vx_tissue_sizes", "vx_tissue_topology",
+                 "vx_batch_destroy", "vx_batch_sizes", "vx_batch_topology",
+                 "vx_min_opts_default", "vx_grad_opts_default"}
+
+
+def test_binding_has_every_entry_point(vx):
+    """The Python binding offers each C entry point under the same name."""
+    from paper_2604_06896_gb300 import _capi
+    for name in set(_capi.EXPORTED) - _HANDLE_LEVEL:
+        assert name in vx.__all__ and callable(getattr(vx, name)), name
+
+
+def test_noalloc_binding_refuses_host_tensors(vx):
+    """No CPU path: host tensors are refused before anything is called."""
+    import torch
+    n = 10
+    he = torch.zeros((6 * n, 8), dtype=torch.int32)
+    fh = torch.zeros(n, dtype=torch.int32)
+    eid = torch.zeros(6 * n, dtype=torch.int32)
+    X = torch.zeros((2 * n, 2), dtype=torch.float64)
+    st = torch.zeros(1, dtype=torch.int32)
+    p = dict(KA=1.0, KP=1.0, A0=1.0, P0=3.7, lam=0.0)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        vx.vx_energy_forces_noalloc(he, fh, eid, 1.0, 1.0, X, p, status=st)
 
 
 @pytest.mark.parametrize("n,stream,aspect", [(10, 61, 1.0), (37, 62, 1.0), (100, 63, 1.0),
