@@ -213,3 +213,37 @@ def test_adjoint_solve_on_an_indefinite_hessian():
 def test_indefinite_planted_mistakes_are_caught(old, new):
     with pytest.raises(AssertionError):
         _check_indefinite_solution(_planted("adjoint_solve", old, new))
+
+
+def test_ep_forward_first_order(equilibrium, ep_grad=None):
+    """The one-sided estimator's error against the adjoint falls ~2x when
+    beta halves (first order in beta), and the centred one beats it at the
+    same beta."""
+    ep_grad = ep_grad or solvers.ep_grad
+    c, t, p, X = equilibrium
+    rng = np.random.default_rng(12)
+    Xt = X + 0.02 * rng.standard_normal(X.shape)
+    gradC = lambda Y: model.cost_v2v(Y, Xt, t)[1]
+    g_adj, _, _ = solvers.adjoint_grad(X, t, p, gradC(X))
+    o = solvers.MinOpts(tol=1e-13, max_iter=100000, dt0=0.01, dt_max=0.5)
+    nrm = np.linalg.norm(g_adj["lam"])
+    errs = []
+    for beta in (0.2, 0.1):
+        g_fw, _ = ep_grad(X, t, p, gradC, beta, o, centered=False)
+        errs.append(np.linalg.norm(g_fw["lam"] - g_adj["lam"]) / nrm)
+    assert 1.6 < errs[0] / errs[1] < 2.5
+    g_c, _ = ep_grad(X, t, p, gradC, 0.1, o, centered=True)
+    assert np.linalg.norm(g_c["lam"] - g_adj["lam"]) / nrm < 0.5 * errs[1]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("return {k: (dp[k] - d0[k]) / beta for k in dp}, (rb,)",
+     "return {k: (dp[k] - d0[k]) / (0.5 * beta) for k in dp}, (rb,)"),
+    ("rb = nudged_relax(Xstar, t, p, cost_grad_fn, beta, opts)",
+     "rb = nudged_relax(Xstar, t, p, cost_grad_fn, -beta, opts)"),
+    ("dp, d0 = model.dE_dtheta(rb.X, t, p), model.dE_dtheta(Xstar, t, p)",
+     "dp, d0 = model.dE_dtheta(rb.X, t, p), model.dE_dtheta(rb.X, t, p)"),
+])
+def test_ep_forward_planted_mistakes_are_caught(equilibrium, old, new):
+    with pytest.raises(AssertionError):
+        test_ep_forward_first_order(equilibrium, ep_grad=_planted("ep_grad", old, new))
