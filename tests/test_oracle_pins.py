@@ -1,5 +1,5 @@
 """Pins of the oracle parts whose mistakes the invariant and FD pins cannot
-see: the FIRE control flow, the T1 decision, the anisotropy magnitude and
+see: the FIRE control flow, the GD step and stop rule, the T1 decision, the anisotropy magnitude and
 the exit-time wrap (CPU only).
 
 * FIRE (Bitzek, Koskinen, Gaehler, Moseler, Gumbsch, PRL 97, 170201, 2006).
@@ -10,6 +10,11 @@ the exit-time wrap (CPU only).
   dt by f_inc (capped at dt_max) and shrinks alpha by f_alpha; P <= 0
   (including the first step, from rest) sets v = 0, dt = f_dec dt,
   alpha = alpha0; then v += dt F and x += dt v.
+* GD and the stop rule (Methods, "Simulation engine"): x += eta F, and the
+  solve stops once max|F| < tol has held for `patience` consecutive
+  iterations (a force above tol restarts the count), checked on a scripted
+  force sequence whose stopping iteration and final position are written
+  out by hand.
 * T1 (Methods, "T1 transitions").  With pure line tension only the four
   edges at the short edge's ends and the edge itself change between the two
   candidates.  For neighbours at distance w along the edge and h across it
@@ -193,6 +198,54 @@ def test_fire_growth_then_alpha_order_planted(monkeypatch):
     bad = planted(solvers, "minimize", src_old, src_new)
     with pytest.raises(AssertionError):
         check_mix(run_scripted(monkeypatch, [(1.0, 0.0)] * 10 + [(1.0, 1.0)], bad), 10)
+
+
+# ---------------------------------------------------- GD step and stop rule
+
+def run_stop_rule(monkeypatch, fmax_seq, patience, minimize=None):
+    """GD (eta = 0.25) on one vertex under the scripted forces (f_k, 0) with
+    tol = 1; returns the result and the number of force evaluations."""
+    calls = []
+
+    def forces(x, t, p):
+        calls.append(x.copy())
+        return np.array([[fmax_seq[min(len(calls) - 1, len(fmax_seq) - 1)], 0.0]])
+
+    monkeypatch.setattr(model, "forces", forces)
+    o = solvers.MinOpts(method="gd", tol=1.0, patience=patience, max_iter=len(fmax_seq) + 5,
+                        gd_lr=0.25)
+    r = (minimize or solvers.minimize)(np.zeros((1, 2)), {}, {}, o)
+    return r, len(calls)
+
+
+STOP_SEQ = [2.0, 0.5, 0.5, 3.0, 0.5, 0.5, 0.5, 0.5]
+
+
+def check_stop_rule(monkeypatch, minimize=None):
+    # patience 3: below tol at iterations 1, 2, then 3.0 resets the count;
+    # 4, 5, 6 make three in a row, so the solve stops at iteration 6 after
+    # six GD steps x += 0.25 f: x = 0.25 (2 + 0.5 + 0.5 + 3 + 0.5 + 0.5)
+    r, n = run_stop_rule(monkeypatch, STOP_SEQ, 3, minimize)
+    assert r.converged and r.iters == 6 and n == 7
+    assert r.X[0, 0] == 1.75 and r.X[0, 1] == 0.0
+    # patience 1 stops at the first force below tol, after one step
+    r, n = run_stop_rule(monkeypatch, STOP_SEQ, 1, minimize)
+    assert r.converged and r.iters == 1 and n == 2 and r.X[0, 0] == 0.5
+
+
+def test_gd_step_and_patience(monkeypatch):
+    check_stop_rule(monkeypatch)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("below = below + 1 if fmax < opts.tol else 0",
+     "below = below + 1 if fmax < opts.tol else below"),
+    ("if below >= opts.patience:", "if below > opts.patience:"),
+    ("x = x + opts.gd_lr * F", "x = x - opts.gd_lr * F"),
+])
+def test_stop_rule_planted_mistakes_are_caught(monkeypatch, old, new):
+    with pytest.raises(AssertionError):
+        check_stop_rule(monkeypatch, planted(solvers, "minimize", old, new))
 
 
 # ----------------------------------------------------------------------- T1
