@@ -16,7 +16,6 @@
 #include <cstring>
 #include <string>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "vx_internal.h"
@@ -36,17 +35,6 @@ struct Corner {       // a polygon corner; edge (k -> k+1) is generated by gen[k
 
 // Key of a Delaunay triangle of the torus: (a, b, sbx, sby, c, scx, scy).
 using Key = std::array<int32_t, 7>;
-
-struct KeyHash {
-  size_t operator()(const Key& k) const {
-    uint64_t h = 1469598103934665603ull;
-    for (int32_t v : k) {
-      h ^= (uint64_t)(uint32_t)v;
-      h *= 1099511628211ull;
-    }
-    return (size_t)h;
-  }
-};
 
 struct Tri {          // three CCW corners (seed, sx, sy)
   int32_t s[3], sx[3], sy[3];
@@ -252,27 +240,48 @@ vx_status build_mesh(const double* seeds, int n, double Lx, double Ly, double* v
       *err = "Voronoi cell of seed " + std::to_string(i) + " could not be built";
       return VX_ERR_DEGENERATE_SEEDS;
     }
-  // Vertices: sorted unique keys.
-  std::vector<Key> keys;
-  keys.reserve(2 * n);
-  for (int i = 0; i < n; ++i)
-    for (const Key& k : cells[i].keys) keys.push_back(k);
-  std::sort(keys.begin(), keys.end());
-  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-  const int V = (int)keys.size();
+  // Vertices: the sorted unique keys.  The order is lexicographic and a
+  // key's first entry is a seed, so a counting sort by that seed followed
+  // by a sort of each (small) bucket gives the sorted order; bstart[a] ..
+  // bstart[a + 1] are then the vertices whose key starts with seed a.
   size_t HE = 0;
   for (int i = 0; i < n; ++i) HE += cells[i].keys.size();
+  std::vector<int32_t> bstart(n + 1, 0);
+  for (int i = 0; i < n; ++i)
+    for (const Key& k : cells[i].keys) bstart[k[0] + 1]++;
+  for (int a = 0; a < n; ++a) bstart[a + 1] += bstart[a];
+  std::vector<Key> keys(HE);
+  {
+    std::vector<int32_t> fill(bstart.begin(), bstart.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (const Key& k : cells[i].keys) keys[fill[k[0]]++] = k;
+  }
+  {
+    size_t w = 0;
+    for (int a = 0; a < n; ++a) {
+      const size_t b0 = bstart[a], b1 = bstart[a + 1];
+      std::sort(keys.begin() + b0, keys.begin() + b1);
+      bstart[a] = (int32_t)w;
+      for (size_t q = b0; q < b1; ++q)
+        if (q == b0 || keys[q] != keys[q - 1]) keys[w++] = keys[q];
+    }
+    bstart[n] = (int32_t)w;
+    keys.resize(w);
+  }
+  const int V = (int)keys.size();
   if (V != 2 * n || HE != (size_t)6 * n) {
     *err = "not a 3-valent torus tessellation (V=" + std::to_string(V) +
            ", HE=" + std::to_string(HE) + ", n=" + std::to_string(n) + ")";
     return VX_ERR_DEGENERATE_SEEDS;
   }
-  std::unordered_map<Key, int32_t, KeyHash> vindex;
-  vindex.reserve(2 * V);
+  auto vertex_of = [&](const Key& k) -> int32_t {
+    for (int32_t v = bstart[k[0]]; v < bstart[k[0] + 1]; ++v)
+      if (keys[v] == k) return v;
+    return -1;
+  };
   std::vector<int32_t> wrapx(V), wrapy(V);
   for (int v = 0; v < V; ++v) {
     const Key& k = keys[v];
-    vindex[k] = v;
     double cx, cy;
     circumcentre(seeds[2 * k[0]], seeds[2 * k[0] + 1],
                  seeds[2 * k[1]] + k[2] * Lx, seeds[2 * k[1] + 1] + k[3] * Ly,
@@ -294,12 +303,11 @@ vx_status build_mesh(const double* seeds, int n, double Lx, double Ly, double* v
     ckx.resize(m);
     cky.resize(m);
     for (int q = 0; q < m; ++q) {
-      auto it = vindex.find(c.keys[q]);
-      if (it == vindex.end()) {
+      cv[q] = vertex_of(c.keys[q]);
+      if (cv[q] < 0) {
         *err = "inconsistent tessellation";
         return VX_ERR_DEGENERATE_SEEDS;
       }
-      cv[q] = it->second;
       ckx[q] = wrapx[cv[q]] + c.tx[q];
       cky[q] = wrapy[cv[q]] + c.ty[q];
     }
@@ -332,36 +340,39 @@ vx_status build_mesh(const double* seeds, int n, double Lx, double Ly, double* v
     }
     h += m;
   }
-  // Twins by (src, tgt, offset).
-  struct HK {
-    int32_t s, t, ox, oy;
-    bool operator==(const HK& o) const { return s == o.s && t == o.t && ox == o.ox && oy == o.oy; }
-  };
-  struct HKH {
-    size_t operator()(const HK& k) const {
-      return ((size_t)(uint32_t)k.s * 0x9E3779B1u) ^ ((size_t)(uint32_t)k.t << 20) ^
-             ((size_t)(k.ox + 1) << 60) ^ ((size_t)(k.oy + 1) << 62);
-    }
-  };
-  std::unordered_map<HK, int32_t, HKH> hidx;
-  hidx.reserve(2 * HE);
-  for (size_t q = 0; q < HE; ++q) {
-    const int32_t* r = he + 8 * q;
-    HK k = {r[3], r[4], r[6], r[7]};
-    if (!hidx.emplace(k, (int32_t)q).second) {
-      *err = "duplicate half-edge";
-      return VX_ERR_DEGENERATE_SEEDS;
-    }
+  // Twins by (src, tgt, offset): the half-edges listed by source vertex
+  // (counting sort), then the twin of s -> t is the half-edge out of t that
+  // points back to s with the opposite offset.
+  std::vector<int32_t> ostart(V + 1, 0), olist(HE);
+  for (size_t q = 0; q < HE; ++q) ostart[he[8 * q + 3] + 1]++;
+  for (int v = 0; v < V; ++v) ostart[v + 1] += ostart[v];
+  {
+    std::vector<int32_t> fill(ostart.begin(), ostart.end() - 1);
+    for (size_t q = 0; q < HE; ++q) olist[fill[he[8 * q + 3]]++] = (int32_t)q;
   }
+  auto same_dir = [&](int32_t p, int32_t q) {
+    const int32_t *a = he + 8 * (size_t)p, *b = he + 8 * (size_t)q;
+    return a[4] == b[4] && a[6] == b[6] && a[7] == b[7];
+  };
+  for (int v = 0; v < V; ++v)
+    for (int32_t x = ostart[v]; x < ostart[v + 1]; ++x)
+      for (int32_t y = x + 1; y < ostart[v + 1]; ++y)
+        if (same_dir(olist[x], olist[y])) {
+          *err = "duplicate half-edge";
+          return VX_ERR_DEGENERATE_SEEDS;
+        }
   for (size_t q = 0; q < HE; ++q) {
     int32_t* r = he + 8 * q;
-    HK k = {r[4], r[3], -r[6], -r[7]};
-    auto it = hidx.find(k);
-    if (it == hidx.end()) {
+    int32_t tw = -1;
+    for (int32_t x = ostart[r[4]]; x < ostart[r[4] + 1] && tw < 0; ++x) {
+      const int32_t* c = he + 8 * (size_t)olist[x];
+      if (c[4] == r[3] && c[6] == -r[6] && c[7] == -r[7]) tw = olist[x];
+    }
+    if (tw < 0) {
       *err = "half-edge without twin";
       return VX_ERR_DEGENERATE_SEEDS;
     }
-    r[2] = it->second;
+    r[2] = tw;
   }
   int32_t e = 0;
   for (size_t q = 0; q < HE; ++q) edge_id[q] = -1;
