@@ -247,3 +247,44 @@ def test_ep_forward_first_order(equilibrium, ep_grad=None):
 def test_ep_forward_planted_mistakes_are_caught(equilibrium, old, new):
     with pytest.raises(AssertionError):
         test_ep_forward_first_order(equilibrium, ep_grad=_planted("ep_grad", old, new))
+
+
+# ------------------------------------- pure line tension (Results, "Energy functions")
+
+def _line_tension_equilibrium(forces=None, monkeypatch=None):
+    """Relax a perturbed honeycomb under pure, uniform line tension and
+    return the largest |sum of the three unit edge vectors| over the
+    vertices, computed from the geometry alone (0 at every vertex of a
+    line-tension equilibrium: three 120-degree angles)."""
+    from oracle.mesh import HE_OFFX, HE_OFFY, HE_SRC, HE_TGT
+    if forces is not None:
+        monkeypatch.setattr(model, "forces", forces)
+    t, _ = honeycomb(6, 6)
+    p = dict(KA=0.0, KP=0.0, A0=1.0, P0=1.0, lam=1.0)
+    s = 1.0 / math.sqrt(3.0)
+    X = t["vert"] + 0.05 * s * np.random.default_rng(5).standard_normal(t["vert"].shape)
+    r = solvers.relax(X, t, p, solvers.MinOpts(tol=1e-11, max_iter=20000, dt0=0.01, dt_max=0.1))
+    assert r.converged
+    he, L = t["he"], np.array([t["Lx"], t["Ly"]])
+    acc = np.zeros_like(r.X)
+    for h in range(he.shape[0]):
+        d = r.X[he[h, HE_TGT]] + he[h, [HE_OFFX, HE_OFFY]] * L - r.X[he[h, HE_SRC]]
+        acc[he[h, HE_SRC]] += d / np.linalg.norm(d)
+    return np.abs(acc).max()
+
+
+def test_pure_line_tension_gives_120_degree_vertices():
+    assert _line_tension_equilibrium() < 1e-9
+
+
+def test_line_tension_planted_mistake_is_caught(monkeypatch):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(model.forces))
+    old = "gl = lam[:, None] * u[rep]"
+    assert src.count(old) == 1
+    ns = dict(vars(model))
+    exec(compile(src.replace(old, "gl = lam[:, None] * u[he[rep, HE_NEXT]]"), "<planted forces>",
+                 "exec"), ns)
+    with pytest.raises(AssertionError):
+        _line_tension_equilibrium(ns["forces"], monkeypatch)
