@@ -2,7 +2,8 @@
 
 Closed forms (regular hexagon, periodic honeycomb), invariants (areas tile
 the box, each edge is in two perimeters, forces sum to zero, translation
-invariance, Hessian symmetry and translation null space), central finite
+invariance, relabelling through permuted seeds, Hessian symmetry and
+translation null space), central finite
 differences, and an independent area formula.  The last tests plant
 plausible mistakes in the oracle and check that these pins catch them.
 """
@@ -73,6 +74,42 @@ def test_invariants(stream):
     shift = np.array([0.3, -0.7])
     assert abs(model.energy(X + shift, t, q) - model.energy(X, t, q)) < 1e-12 * abs(model.energy(X, t, q))
     assert np.abs(model.forces(X + shift, t, q) - F).max() < 1e-11 * np.abs(F).max()
+
+
+def _match(P, Q, L):
+    """Index map m with Q[m[i]] == P[i] (points wrapped into the box)."""
+    key = lambda Z: [tuple(np.round(np.mod(z, L) / L * 1e9).astype(np.int64)) for z in Z]
+    kq = {k: j for j, k in enumerate(key(Q))}
+    return np.array([kq[k] for k in key(P)])
+
+
+def test_relabelling_invariance():
+    """Building from permuted seeds gives the same tissue under other labels:
+    the same energy, areas and forces carried by the matching cells and
+    vertices, with per-cell and per-edge parameters moved along."""
+    c, t, p = tissue(40, 35)
+    rng = np.random.default_rng(35)
+    q = hetero(t, p, rng)
+    q["lam"] = rng.uniform(0.02, 0.1, 3 * t["n"])
+    pi = rng.permutation(t["n"])
+    t2 = mesh.build_periodic_voronoi(c["seeds"][pi], c["Lx"], c["Ly"])
+    L = np.array([c["Lx"], c["Ly"]])
+    vm = _match(t["vert"], t2["vert"], L)            # vertex i -> vertex vm[i] of t2
+    def mids(tt):
+        rep = model.edge_rep(tt)
+        d = model.geometry(tt["vert"], tt)["d"][rep]
+        return tt["vert"][tt["he"][rep, HE_SRC]] + 0.5 * d
+    em = _match(mids(t), mids(t2), L)               # edge e -> edge em[e] of t2
+    q2 = {k: (v[pi] if np.ndim(v) else v) for k, v in q.items() if k != "lam"}
+    lam2 = np.empty_like(q["lam"])
+    lam2[em] = q["lam"]
+    q2["lam"] = lam2
+    E1, E2 = model.energy(t["vert"], t, q), model.energy(t2["vert"], t2, q2)
+    assert abs(E1 - E2) < 1e-12 * abs(E1)
+    A1, A2 = model.geometry(t["vert"], t)["A"], model.geometry(t2["vert"], t2)["A"]
+    assert np.abs(A2 - A1[pi]).max() < 1e-12 * np.abs(A1).max()
+    F1, F2 = model.forces(t["vert"], t, q), model.forces(t2["vert"], t2, q2)
+    assert np.abs(F2[vm] - F1).max() < 1e-10 * np.abs(F1).max()
 
 
 def test_area_independent_formula():
