@@ -136,3 +136,56 @@ def test_batch_autotune(vx):
     rs = vx.vx_minimize_batched(b, X, params, **kw)
     assert all(r.status in (0, 1) for r in rs)
     b.close()
+
+
+def c3_sample(ns):
+    """The tissues whose outputs the oracle recomputes: the smallest, the
+    largest and every 64th."""
+    ns = np.asarray(ns)
+    return sorted({int(np.argmin(ns)), int(np.argmax(ns))} | set(range(0, len(ns), 64)))
+
+
+def check_c3_outputs(batch, results, Xs, tops, sample):
+    """Every tissue ends with a solver status; on the sampled tissues the
+    oracle's energy and max|F| at the returned state (positions and
+    topology) match what the GPU reported, the topology is a valid periodic
+    half-edge mesh and the areas tile the box."""
+    assert len(results) == len(batch)
+    assert all(r.status in (0, 1) for r in results)
+    for k in sample:
+        c, r, X, top = batch[k], results[k], Xs[k], dict(tops[k])
+        t = dict(top, vert=X)
+        check_half_edge_invariants(t)
+        p = dict(KA=1.0, KP=1.0, A0=1.0, P0=c["P0"], lam=c["lam"])
+        F = omodel.forces(X, t, p)
+        fo = float(np.sqrt((F * F).sum(axis=1)).max())
+        E = omodel.energy(X, t, p)
+        A = omodel.geometry(X, t)["A"]
+        print(f"c3 tissue {k} n={c['n']}: status {r.status} it {r.iters} T1 {r.n_t1} "
+              f"fmax {r.fmax:.2e} oracle {fo:.2e} dE/E {abs(r.energy - E) / abs(E):.1e}")
+        assert abs(A.sum() - c["Lx"] * c["Ly"]) < 1e-9 * c["Lx"] * c["Ly"]
+        assert abs(r.energy - E) < 1e-5 * abs(E)
+        assert fo < 2e-6 + 2 * r.fmax
+
+
+def test_batch_c3_full_size(vx):
+    """The batched forward workload at full size, in the launch the
+    benchmark times: 512 tissues of 200-5,000 cells (7.5e5 cells), FP32,
+    FIRE + T1 to max|F| < 1e-6 with a 20,000-iteration budget, small tissues
+    on CTAs and large ones on 8-CTA clusters in one graph-replayed launch;
+    sampled tissues checked against the oracle."""
+    import torch
+    batch = vi.batch_c3()
+    meshes = [vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]) for c in batch]
+    b = vx.Batch(meshes, "f32")
+    X = torch.tensor(np.concatenate([m["vert"] for m in meshes]), dtype=torch.float64,
+                     device="cuda")
+    lam = torch.tensor(np.concatenate([c["lam"] for c in batch]), device="cuda")
+    prm = dict(KA=1.0, KP=1.0, A0=1.0, P0=np.array([c["P0"] for c in batch]), lam=lam)
+    rs = vx.vx_minimize_batched(b, X, prm, tol=1e-6, max_iter=20_000, dt0=0.01, dt_max=0.5,
+                                l_min=5e-3)
+    tops = b.topologies()
+    Xs = b.split(X.cpu().numpy())
+    print(f"c3: {sum(r.status == 0 for r in rs)} of {len(rs)} tissues converged")
+    check_c3_outputs(batch, rs, Xs, tops, c3_sample([c["n"] for c in batch]))
+    b.close()
