@@ -167,3 +167,67 @@ def test_seed_order_is_a_locality_permutation(vx):
     r1 = omesh.build_periodic_voronoi(c["seeds"], c["Lx"], c["Ly"])
     a1 = omodel.geometry(r1["vert"], r1)["A"]
     assert np.allclose(a0, a1[order], rtol=1e-12)
+
+
+def _create(he, face_he, edge_id, n, Lx, Ly, dtype=0):
+    """vx_tissue_create through the raw ABI; the table checks run on the host
+    before any device call, so malformed tables are refused without a GPU."""
+    import ctypes as C
+    from paper_2604_06896_gb300 import _capi
+    he = np.ascontiguousarray(he, dtype=np.int32)
+    fh = np.ascontiguousarray(face_he, dtype=np.int32)
+    eid = np.ascontiguousarray(edge_id, dtype=np.int32)
+    h = C.c_void_p()
+    st = _capi.vx_tissue_create(he.ctypes.data, fh.ctypes.data, eid.ctypes.data, n, he.shape[0],
+                                Lx, Ly, dtype, None, C.byref(h))
+    return st, _capi.vx_last_error().decode()
+
+
+def _malformed_cases(m):
+    """(name, he, face_he, edge_id, expected message) from one valid mesh."""
+    he, fh, eid = m["he"], m["face_he"], m["edge_id"]
+    HE = he.shape[0]
+    out = []
+    a = he.copy(); a[3, 1] = HE
+    out.append(("next out of range", a, fh, eid, "index out of range"))
+    a = he.copy(); a[5, 5] = m["n"]
+    out.append(("face out of range", a, fh, eid, "face out of range"))
+    a = he.copy(); a[7, 6] = 2
+    out.append(("offset 2", a, fh, eid, "offsets must be in"))
+    e = eid.copy(); e[4] = HE // 2
+    out.append(("edge id out of range", he, fh, e, "edge_id out of range"))
+    a = he.copy(); a[9, 2] = 9
+    out.append(("twin of itself", a, fh, eid, "twin is not an involution"))
+    # a half-edge whose offset is not the negated offset of its twin's
+    h = int(np.nonzero(he[:, 6] != 0)[0][0])
+    a = he.copy(); a[h, 6] = 0
+    out.append(("twin offsets", a, fh, eid, "twin offsets must be negated"))
+    # the offsets of one edge changed on both half-edges: twins agree, the
+    # two faces' offset sums no longer vanish
+    h = int(np.nonzero((he[:, 6] == 0) & (he[:, 7] == 0))[0][0])
+    a = he.copy(); a[h, 7] = 1; a[he[h, 2], 7] = -1
+    out.append(("face offsets", a, fh, eid, "do not cancel"))
+    # prev pointers of two half-edges exchanged
+    a = he.copy(); a[[0, 10], 0] = a[[10, 0], 0]
+    out.append(("prev(next(h))", a, fh, eid, "prev(next(h)) != h"))
+    # edge ids of two half-edges of different edges exchanged
+    h2 = next(q for q in range(1, HE) if eid[q] != eid[0] and he[0, 2] != q)
+    e = eid.copy(); e[[0, h2]] = e[[h2, 0]]
+    out.append(("edge ids", he, fh, e, "twins must share an edge id"))
+    f = fh.copy(); f[0] = fh[1]
+    out.append(("face_he", he, f, eid, "face_he[0]"))
+    return out
+
+
+def test_tissue_create_refuses_malformed_tables(vx):
+    c = vi.small_tissue(20, 64)
+    m = vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"])
+    for name, he, fh, eid, msg in _malformed_cases(m):
+        st, err = _create(he, fh, eid, m["n"], m["Lx"], m["Ly"])
+        assert st == 2 and msg in err, (name, st, err)
+    st, err = _create(m["he"][:-6], m["face_he"], m["edge_id"][:-6], m["n"], m["Lx"], m["Ly"])
+    assert st == 2 and "6 n half-edges" in err
+    st, err = _create(m["he"], m["face_he"], m["edge_id"], m["n"], m["Lx"], m["Ly"], dtype=7)
+    assert st == 2 and "dtype" in err
+    st, err = _create(m["he"], m["face_he"], m["edge_id"], m["n"], 0.0, m["Ly"])
+    assert st == 2 and "box" in err
