@@ -231,3 +231,27 @@ def test_tissue_create_refuses_malformed_tables(vx):
     assert st == 2 and "dtype" in err
     st, err = _create(m["he"], m["face_he"], m["edge_id"], m["n"], 0.0, m["Ly"])
     assert st == 2 and "box" in err
+
+
+def test_option_defaults_through_the_binding(vx):
+    """The defaults the library fills in reach Python field by field (the
+    ctypes structs match vx.h's layout), and FIRE's constants are the
+    oracle's (Bitzek et al.: N_min 5, f_inc 1.1, f_dec 0.5, alpha0 0.1,
+    f_alpha 0.99), which the same-trajectory parity tests rely on."""
+    import ctypes as C
+    from oracle import solvers
+    from paper_2604_06896_gb300 import _capi
+    o = _capi.vx_min_opts()
+    _capi.vx_min_opts_default(C.byref(o))
+    assert (o.method, o.tol, o.patience, o.max_iter, o.gd_lr) == (vx.VX_FIRE, 1e-8, 1, 100000, 1e-2)
+    assert (o.dt0, o.dt_max, o.l_min, o.path, o.check_every) == (0.01, 0.5, 0.0, vx.VX_PATH_AUTO, 50)
+    assert (o.wrap, o.refine_tol) == (1, 0.0) and not o.edge_events
+    ref = solvers.MinOpts()
+    assert (o.n_min, o.f_inc, o.f_dec, o.alpha0, o.f_alpha) == \
+        (ref.n_min, ref.f_inc, ref.f_dec, ref.alpha0, ref.f_alpha)
+    g = _capi.vx_grad_opts()
+    _capi.vx_grad_opts_default(C.byref(g))
+    assert (g.mode, g.beta, g.cg_rtol, g.cg_max_iter, g.cost) == \
+        (vx.VX_ADJOINT_CG, 1e-3, 1e-10, 20000, vx.VX_COST_NONE)
+    assert not g.cost_data and g.ep_f64 == 1
+    assert (g.inner.tol, g.inner.n_min, g.inner.wrap) == (1e-10, 5, 1)
