@@ -1011,29 +1011,29 @@ vx_status vx_batch_create(int32_t count, const int32_t* n_cells, const double* b
   size_t hoff = 0, coff = 0;
   for (int k = 0; k < count; ++k) {
     const int n = n_cells[k], HE = 6 * n, V = 2 * n, E = 3 * n;
-    if (n < 1 || n > (INT32_MAX - hb) / 6) {
+    if (n < 1 || n > (1 << 24) || n > (INT32_MAX - hb) / 6) {
       delete b;
-      return fail(VX_ERR_INVALID_ARG, n < 1 ? "every tissue needs cells"
-                                            : "the batch holds more than 2^31 half-edges");
+      return fail(VX_ERR_INVALID_ARG, n < 1           ? "every tissue needs cells"
+                                      : n > (1 << 24) ? "n_cells too large"
+                                                      : "the batch holds more than 2^31 half-edges");
     }
-    vx_tissue t = nullptr;
-    // host-only validation and internal tables via vx_tissue_create would
-    // allocate device memory per tissue; instead reuse its table logic:
-    const vx_status st = vx_tissue_create(he + 8 * hoff, face_he + coff, edge_id + hoff, n, HE,
-                                          box[2 * k], box[2 * k + 1], dtype, stream, &t);
-    if (st != VX_OK) {
+    // the single-tissue checks and internal tables, on the host only
+    const double Lx = box[2 * k], Ly = box[2 * k + 1];
+    if (!(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly)) {
       delete b;
-      return st;
+      return fail(VX_ERR_INVALID_ARG, "tissue " + std::to_string(k) +
+                                          ": box sides must be positive and finite");
     }
-    std::vector<uint32_t> t_tgt(HE);
-    std::vector<int32_t> t_nxt(HE), t_face(HE), t_vout(3 * V), t_ff(n);
-    cudaMemcpy(t_tgt.data(), t->tgt, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
-    cudaMemcpy(t_nxt.data(), t->nxt, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
-    cudaMemcpy(t_face.data(), t->face, 4 * (size_t)HE, cudaMemcpyDeviceToHost);
-    cudaMemcpy(t_vout.data(), t->vout, 12 * (size_t)V, cudaMemcpyDeviceToHost);
-    cudaMemcpy(t_ff.data(), t->ffirst, 4 * (size_t)n, cudaMemcpyDeviceToHost);
-    b->int2ext.push_back(t->int2ext);
-    vx_tissue_destroy(t);
+    vx::HostTables ht;
+    const std::string m = vx::build_host_tables(he + 8 * hoff, face_he + coff, edge_id + hoff, n,
+                                                HE, &ht);
+    if (!m.empty()) {
+      delete b;
+      return fail(VX_ERR_INVALID_ARG, "tissue " + std::to_string(k) + ": " + m);
+    }
+    const std::vector<uint32_t>& t_tgt = ht.tgt;
+    const std::vector<int32_t>&t_nxt = ht.nxt, &t_face = ht.face, &t_vout = ht.vout, &t_ff = ht.ff;
+    b->int2ext.push_back(std::move(ht.int2ext));
     tgt.insert(tgt.end(), t_tgt.begin(), t_tgt.end());
     nxt.insert(nxt.end(), t_nxt.begin(), t_nxt.end());
     face.insert(face.end(), t_face.begin(), t_face.end());

@@ -125,6 +125,66 @@ vx::ParamsD to_params(const vx_params* p) {
 
 }  // namespace
 
+namespace vx {
+
+std::string build_host_tables(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                              int n, int HE, HostTables* ht) {
+  const std::string m = check_tables(he, face_he, edge_id, n, HE);
+  if (!m.empty()) return m;
+  const int V = HE / 3;
+  std::vector<int32_t>& ext2int = ht->ext2int;
+  std::vector<int32_t>& int2ext = ht->int2ext;
+  ext2int.assign(HE, 0);
+  int2ext.assign(HE, 0);
+  for (int h = 0; h < HE; ++h) {
+    const int tw = he[8 * h + 2];
+    const int hi = 2 * edge_id[h] + (h > tw ? 1 : 0);
+    ext2int[h] = hi;
+    int2ext[hi] = h;
+  }
+  std::vector<uint32_t>& tgt = ht->tgt;
+  std::vector<int32_t>&nxt = ht->nxt, &face = ht->face, &vout = ht->vout, &ff = ht->ff;
+  tgt.assign(HE, 0u);
+  nxt.assign(HE, 0);
+  face.assign(HE, 0);
+  vout.assign(3 * (size_t)V, -1);
+  ff.assign(n, 0);
+  std::vector<int> firstout(V, -1);
+  for (int hc = 0; hc < HE; ++hc) {
+    const int32_t* r = he + 8 * hc;
+    const int hi = ext2int[hc];
+    tgt[hi] = pack_tgt(r[4], r[6], r[7]);
+    nxt[hi] = ext2int[r[1]];
+    face[hi] = r[5];
+    const int s = r[3];
+    if (firstout[s] < 0 || hi < firstout[s]) firstout[s] = hi;
+  }
+  // Out-lists in counter-clockwise order: h, twin(prev(h)), twin(prev(.)).
+  for (int v = 0; v < V; ++v) {
+    int h = firstout[v];
+    for (int a = 0; a < 3; ++a) {
+      vout[a * V + v] = h;
+      const int hp = ext2int[he[8 * int2ext[h] + 0]];
+      h = hp ^ 1;
+    }
+    if (h != firstout[v]) return "vertex " + std::to_string(v) + ": out-half-edges do not close";
+  }
+  for (int c = 0; c < n; ++c) ff[c] = ext2int[face_he[c]];
+  for (int c = 0; c < n; ++c) {
+    int h = ff[c], k = 0;
+    do {
+      ++k;
+      h = nxt[h];
+    } while (h != ff[c] && k <= kMaxCorners);
+    if (k > kMaxCorners - 1)
+      return "cell " + std::to_string(c) + " has more than " + std::to_string(kMaxCorners - 1) +
+             " edges";
+  }
+  return "";
+}
+
+}  // namespace vx
+
 extern "C" {
 
 const char* vx_last_error(void) { return vx::g_err.c_str(); }
@@ -165,7 +225,8 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   if (!(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
     return invalid("box sides must be positive and finite");
   if (n_cells > (1 << 24)) return invalid("n_cells too large");
-  const std::string m = check_tables(he, face_he, edge_id, n_cells, n_half_edges);
+  vx::HostTables ht;
+  const std::string m = vx::build_host_tables(he, face_he, edge_id, n_cells, n_half_edges, &ht);
   if (!m.empty()) return invalid(m);
   const int n = n_cells, HE = n_half_edges, V = HE / 3, E = HE / 2;
   vx_tissue_s* t = new vx_tissue_s();
@@ -177,52 +238,10 @@ vx_status vx_tissue_create(const int32_t* he, const int32_t* face_he, const int3
   t->Lx = Lx;
   t->Ly = Ly;
   t->dtype = dtype;
-  t->ext2int.resize(HE);
-  t->int2ext.resize(HE);
-  for (int h = 0; h < HE; ++h) {
-    const int tw = he[8 * h + 2];
-    const int hi = 2 * edge_id[h] + (h > tw ? 1 : 0);
-    t->ext2int[h] = hi;
-    t->int2ext[hi] = h;
-  }
-  std::vector<uint32_t> tgt(HE);
-  std::vector<int32_t> nxt(HE), face(HE), vout(3 * V, -1), ff(n);
-  std::vector<int> firstout(V, -1);
-  for (int hc = 0; hc < HE; ++hc) {
-    const int32_t* r = he + 8 * hc;
-    const int hi = t->ext2int[hc];
-    tgt[hi] = vx::pack_tgt(r[4], r[6], r[7]);
-    nxt[hi] = t->ext2int[r[1]];
-    face[hi] = r[5];
-    const int s = r[3];
-    if (firstout[s] < 0 || hi < firstout[s]) firstout[s] = hi;
-  }
-  // Out-lists in counter-clockwise order: h, twin(prev(h)), twin(prev(.)).
-  for (int v = 0; v < V; ++v) {
-    int h = firstout[v];
-    for (int a = 0; a < 3; ++a) {
-      vout[a * V + v] = h;
-      const int hp = t->ext2int[he[8 * t->int2ext[h] + 0]];
-      h = hp ^ 1;
-    }
-    if (h != firstout[v]) {
-      delete t;
-      return invalid("vertex " + std::to_string(v) + ": out-half-edges do not close");
-    }
-  }
-  for (int c = 0; c < n; ++c) ff[c] = t->ext2int[face_he[c]];
-  for (int c = 0; c < n; ++c) {
-    int h = ff[c], k = 0;
-    do {
-      ++k;
-      h = nxt[h];
-    } while (h != ff[c] && k <= vx::kMaxCorners);
-    if (k > vx::kMaxCorners - 1) {
-      delete t;
-      return invalid("cell " + std::to_string(c) + " has more than " +
-                     std::to_string(vx::kMaxCorners - 1) + " edges");
-    }
-  }
+  t->ext2int = std::move(ht.ext2int);
+  t->int2ext = std::move(ht.int2ext);
+  const std::vector<uint32_t>& tgt = ht.tgt;
+  const std::vector<int32_t>&nxt = ht.nxt, &face = ht.face, &vout = ht.vout, &ff = ht.ff;
   auto bytes = [](size_t b) { return b < 16 ? (size_t)16 : b; };
   const int nbc = (n + 255) / 256 + 1, nbv = (V + 255) / 256 + 1;
   cudaError_t e = cudaSuccess;

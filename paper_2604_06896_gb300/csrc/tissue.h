@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "device_math.cuh"
@@ -46,6 +47,21 @@ struct vx_tissue_s {
 };
 
 namespace vx {
+// The internal tables of one tissue, built on the host from the caller's
+// half-edge tables: the internal numbering (edge e owns half-edges 2e and
+// 2e + 1, the caller's smaller index first) both ways, packed targets,
+// next, face, the counter-clockwise out-lists [3][V] and each face's first
+// half-edge.
+struct HostTables {
+  std::vector<int32_t> ext2int, int2ext;
+  std::vector<uint32_t> tgt;
+  std::vector<int32_t> nxt, face, vout, ff;
+};
+// Validates the caller's tables and builds the internal ones (host only, no
+// device call); returns "" or the reason the tables are refused.
+std::string build_host_tables(const int32_t* he, const int32_t* face_he, const int32_t* edge_id,
+                              int n, int HE, HostTables* ht);
+
 // The float64 workspace `work`, allocated once by vx_tissue_create, in three
 // regions that calls use at the same time without overlap:
 //   solver: CG vectors of the plain adjoint (x, r, p, h, 2x2 blocks), the
