@@ -255,3 +255,27 @@ def test_option_defaults_through_the_binding(vx):
         (vx.VX_ADJOINT_CG, 1e-3, 1e-10, 20000, vx.VX_COST_NONE)
     assert not g.cost_data and g.ep_f64 == 1
     assert (g.inner.tol, g.inner.n_min, g.inner.wrap) == (1e-10, 5, 1)
+
+
+def test_batch_create_names_the_malformed_tissue(vx):
+    """vx_batch_create checks every member's tables on the host before any
+    device allocation and names the first member it refuses."""
+    import ctypes as C
+    from paper_2604_06896_gb300 import _capi
+    ms = []
+    for n, st in ((60, 65), (40, 66), (30, 67)):
+        c = vi.small_tissue(n, st)
+        ms.append(vx.vx_build_mesh(c["seeds"], c["Lx"], c["Ly"]))
+    bad = _malformed_cases(ms[1])[0]            # next out of range
+    tables = [(m["he"], m["face_he"], m["edge_id"]) for m in ms]
+    tables[1] = bad[1:4]
+    n = np.array([m["n"] for m in ms], dtype=np.int32)
+    box = np.ascontiguousarray([[m["Lx"], m["Ly"]] for m in ms], dtype=np.float64)
+    he, fh, eid = (np.ascontiguousarray(np.concatenate([t[i] for t in tables]), dtype=np.int32)
+                   for i in range(3))
+    h = C.c_void_p()
+    st = _capi.vx_batch_create(3, n.ctypes.data, box.ctypes.data, he.ctypes.data, fh.ctypes.data,
+                               eid.ctypes.data, 1, None, C.byref(h))
+    err = _capi.vx_last_error().decode()
+    assert st == 2 and err.startswith("tissue 1: ") and "index out of range" in err
+    assert h.value is None
