@@ -328,6 +328,17 @@ def c4_oracle_errors(check):
                     "pipeline is measured by tests/test_gpu_c4.py"}
 
 
+def status_counts(results):
+    """How many tissues ended with each vx_status (0 converged, 1 out of
+    budget, higher an error), keyed by the status name."""
+    names = {0: "ok", 1: "not_converged", 4: "cuda", 8: "nonfinite", 9: "topology"}
+    out = {}
+    for r in results:
+        k = names.get(int(r.status), str(int(r.status)))
+        out[k] = out.get(k, 0) + 1
+    return out
+
+
 def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, compare=True,
                            dist=None):
     """The batched forward workload: 512 periodic Voronoi tissues of
@@ -388,6 +399,7 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, c
     if not compare:
         return {"metric": "vertex-force evals/s", "value": value, "ms_per_step": ms_step,
                 "converged": int(sum(r.status == 0 for r in rs)),
+                "status_counts": status_counts(rs),
                 "force_evals_per_tissue": [int(min(r.force_evals for r in rs)),
                                            int(max(r.force_evals for r in rs))]}
     sub = allidx[::subset_every]
@@ -416,6 +428,7 @@ def batched_forward_metric(vx, torch, steps, subset_every=32, max_iter=20_000, c
                         f"p0 ~ U(3.5,4.0), Lambda ~ U(0,0.1), A0 = 1, FP32, FIRE+T1 to max|F|<1e-6, "
                         f"{max_iter}-iteration budget, one graph-replayed persistent launch",
             "converged": int(sum(r.status == 0 for r in rs)),
+            "status_counts": status_counts(rs),
             "force_evals_per_tissue": [int(min(r.force_evals for r in rs)),
                                        int(max(r.force_evals for r in rs))],
             "subset": {"tissues": len(sub), "batched_value": sub_value, "batched_ms": sub_ms,
