@@ -498,6 +498,7 @@ def batched_gradient_metric(vx, torch, free_iters=5000, plain_tissues=None, comp
                         f"({free_iters}-iteration budget), anisotropy cost, adjoint gradient for "
                         f"per-cell A0 and per-edge Lambda (CG rtol 1e-6), one launch",
             "free_converged": int(sum(r[0].status == 0 for r in rs)),
+            "free_status_counts": status_counts([r[0] for r in rs]),
             "cg_iters": [int(min(r[1].cg_iters for r in rs)), int(max(r[1].cg_iters for r in rs))],
             "plain_gpu_path": {"value": v_p, "tissues": len(idx), "ms": ms_p},
             "vs_plain_gpu_path": v_b / v_p}
