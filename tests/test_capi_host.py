@@ -105,6 +105,41 @@ def test_mesh_bit_exact_many_seed_sets(vx):
     assert agree > 700
 
 
+def test_mesh_degenerate_verdicts_agree(vx):
+    """Adversarial seed sets: coincident seeds and cocircular quadruples on
+    coarse grids, square lattices (every Delaunay triangle ambiguous) and
+    seeds crowded into a strip.  Both builders refuse the same sets and give
+    the same tables and positions for the others."""
+    rng = np.random.default_rng(0)
+    seen = set()
+    for k in range(150):
+        n = int(rng.integers(4, 80))
+        Lx, Ly = float(rng.uniform(1, 3)), float(rng.uniform(1, 3))
+        if k % 3 == 0:
+            g = int(rng.integers(3, 9))
+            s = np.stack([rng.integers(0, g, n) * Lx / g, rng.integers(0, g, n) * Ly / g], 1)
+        elif k % 3 == 1:
+            m = int(np.ceil(np.sqrt(n)))
+            i = np.arange(n)
+            s = np.stack([(i % m + 0.5) * Lx / m, (i // m % m + 0.5) * Ly / m], 1)
+        else:
+            s = np.stack([rng.uniform(0, 0.2 * Lx, n), rng.uniform(0, Ly, n)], 1)
+        try:
+            ref = omesh.build_periodic_voronoi(s, Lx, Ly)
+        except omesh.DegenerateSeeds:
+            ref = None
+        try:
+            got = vx.vx_build_mesh(s, Lx, Ly)
+        except vx.VxError:
+            got = None
+        assert (ref is None) == (got is None), (k, n)
+        seen.add(ref is None)
+        if ref is not None:
+            for key in ("he", "face_he", "edge_id", "vert"):
+                assert np.array_equal(got[key], ref[key]), (k, key)
+    assert seen == {True, False}
+
+
 @pytest.mark.parametrize("case", ["c2", "c2_hilbert", "n5000"])
 def test_mesh_bit_exact_full_size(vx, case):
     """The 10,000-cell tissue the benchmark builds (in the given seed order
